@@ -1,0 +1,162 @@
+"""FP64 CPU oracle for the coupled mode equations (CMEs).
+
+TEST INFRASTRUCTURE ONLY: imported by `tests/`, by `__graft_entry__.smoke()` and by the
+CPU-baseline leg of `bench.py`, never by the product package.  It shares no code with the
+CUDA path.
+
+Two engines:
+  * `direct` (C library `cme_oracle.c`): the four-wave-mixing sum as the direct O(N^3)
+    triple sum of Eq. 2 / Eq. 3, RK4IP / Strang / plain RK4 steps in textbook order, naive
+    O(N^2) transforms over the mode number.  This is the definition.
+  * `fft_engine` (numpy): the same integrators with the FWM sum evaluated through Eq. 4 using
+    numpy.fft as a library primitive; used only where O(N^3) is infeasible, and pinned to the
+    direct engine by the tests.
+
+Layout: arrays hold modes in centred order, index i <-> mu = i - N/2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libcme_oracle.so")
+_SRC = os.path.join(_HERE, "cme_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+RK4IP, STRANG, RK4 = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (plain -O2, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=gnu11", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            dp = ctypes.POINTER(ctypes.c_double)
+            c_int, c_long, c_double = ctypes.c_int, ctypes.c_long, ctypes.c_double
+            lib.oracle_fwm.argtypes = [c_int, c_int, dp, dp]
+            lib.oracle_rhs.argtypes = [c_int, c_int, c_double, c_double, c_double, c_double, dp, dp]
+            lib.oracle_integrate.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double,
+                                             c_double, c_double, c_double, c_double, c_long, dp]
+            lib.oracle_integrate_eq1.argtypes = [c_int, c_int, dp, dp, c_double, c_double,
+                                                 c_double, c_double, c_double, c_double,
+                                                 c_double, c_long, dp]
+            lib.oracle_dft.argtypes = [c_int, c_int, dp, dp]
+            lib.oracle_invariants.argtypes = [c_int, c_int, dp, c_double, c_double, dp, dp]
+            for name in ("oracle_fwm", "oracle_rhs", "oracle_integrate", "oracle_integrate_eq1",
+                         "oracle_dft", "oracle_invariants"):
+                getattr(lib, name).restype = c_int
+            _lib = lib
+    return _lib
+
+
+def _cbuf(z) -> np.ndarray:
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+    return np.ascontiguousarray(z.view(np.float64).copy())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ValueError(f"oracle call failed with code {rc}")
+
+
+def fwm(D, linear: bool = False) -> np.ndarray:
+    """Direct FWM sum (Eq. 2 / Eq. 3) of a centred complex vector."""
+    d = _cbuf(D)
+    N = d.size // 2
+    out = np.empty_like(d)
+    _check(_load().oracle_fwm(N, int(linear), _dp(d), _dp(out)))
+    return out.view(np.complex128)
+
+
+def rhs(D, g0: float, kappa_ext: float, A_in: complex, linear: bool = False) -> np.ndarray:
+    """F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D)."""
+    d = _cbuf(D)
+    N = d.size // 2
+    out = np.empty_like(d)
+    _check(_load().oracle_rhs(N, int(linear), g0, kappa_ext, complex(A_in).real,
+                              complex(A_in).imag, _dp(d), _dp(out)))
+    return out.view(np.complex128)
+
+
+def integrate(inst, h: float, nsteps: int, method: int = RK4IP, linear: bool = False,
+              D=None) -> np.ndarray:
+    """Advance one instance (workloads.Instance-like) by nsteps of the chosen integrator.
+    Returns the final field in the rotating (D) frame, centred order."""
+    d = _cbuf(inst.D0 if D is None else D)
+    kap = np.ascontiguousarray(inst.kappa, dtype=np.float64)
+    om = np.ascontiguousarray(inst.omega, dtype=np.float64)
+    A = complex(inst.A_in)
+    _check(_load().oracle_integrate(method, inst.N, int(linear), _dp(kap), _dp(om), inst.g0,
+                                    inst.kappa_ext, A.real, A.imag, inst.sigma, h, int(nsteps),
+                                    _dp(d)))
+    return d.view(np.complex128)
+
+
+def integrate_eq1(inst, tau0: float, h: float, nsteps: int, A=None, linear: bool = False):
+    """Classic RK4 on Eq. 1 as printed (laboratory frame, explicit phase factors)."""
+    a = _cbuf(inst.D0 if A is None else A)
+    kap = np.ascontiguousarray(inst.kappa, dtype=np.float64)
+    om = np.ascontiguousarray(inst.omega, dtype=np.float64)
+    Ain = complex(inst.A_in)
+    _check(_load().oracle_integrate_eq1(inst.N, int(linear), _dp(kap), _dp(om), inst.g0,
+                                        inst.kappa_ext, Ain.real, Ain.imag, inst.sigma, tau0, h,
+                                        int(nsteps), _dp(a)))
+    return a.view(np.complex128)
+
+
+def dft(x, sign: int) -> np.ndarray:
+    """Naive transform over the mode number: sign=+1 modes -> time, sign=-1 time -> modes."""
+    d = _cbuf(x)
+    N = d.size // 2
+    out = np.empty_like(d)
+    _check(_load().oracle_dft(N, sign, _dp(d), _dp(out)))
+    return out.view(np.complex128)
+
+
+def invariants(D, omega, g0: float, sigma: float, linear: bool = False):
+    """(sum |D|^2, H) of the lossless, unpumped system."""
+    d = _cbuf(D)
+    N = d.size // 2
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    out = np.empty(2)
+    _check(_load().oracle_invariants(N, int(linear), _dp(om), g0, sigma, _dp(d), _dp(out)))
+    return float(out[0]), float(out[1])
+
+
+def to_lab_frame(inst, D, tau: float) -> np.ndarray:
+    """A_mu = D_mu exp(-i (omega_mu - omega_0 - sigma) tau)."""
+    om = np.asarray(inst.omega, dtype=np.float64)
+    ph = (om - om[inst.N // 2] - inst.sigma) * tau
+    return np.asarray(D) * np.exp(-1j * ph)
+
+
+def rel_l2(x, y) -> float:
+    """||x - y||_2 / ||y||_2 over all modes."""
+    x = np.asarray(x)
+    y = np.asarray(y)
+    return float(np.linalg.norm(x - y) / np.linalg.norm(y))

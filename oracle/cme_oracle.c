@@ -1,0 +1,396 @@
+/*
+ * FP64 CPU oracle for the coupled mode equations (CMEs) of Kerr comb generation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load this library.  It shares no code with the CUDA path.
+ *
+ * Everything here is the plain definition, written for reading, not for speed:
+ *   - the four-wave-mixing (FWM) sum is the direct triple sum of Eq. 2 / Eq. 3,
+ *     O(N^3) per evaluation (the cost analysed in Sec. 2 of the paper);
+ *   - transforms, where the Strang splitting needs the time-domain field, are the naive
+ *     O(N^2) sums over the mode number mu of Eq. 4;
+ *   - RK4IP (fourth-order Runge-Kutta in the interaction picture), the Strang split step
+ *     and plain RK4 take their steps in the textbook order.
+ *
+ * Layout: every complex array holds modes in centred order, index i <-> mu = i - N/2.
+ *
+ * Model (Eq. 1 written in the frame D_mu = A_mu exp(i (omega_mu - omega_0 - sigma) tau),
+ * which removes every explicit time dependence of Eq. 1 because alpha - beta + gamma = mu):
+ *     dD_mu/dtau = L_mu D_mu + F_mu(D),
+ *     L_mu = -kappa_mu/2 + i (omega_mu - omega_0 - sigma),
+ *     F_mu(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM_mu(D),
+ *     FWM_mu(D) = sum_{alpha - beta + gamma = mu} D_alpha conj(D_beta) D_gamma.
+ * The constraint alpha - beta + gamma = mu is taken modulo N ("circular", the reading that
+ * matches Eq. 4 with an N-point transform) or literally ("linear", no wrap-around).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL -1
+
+/* centred index of mode mu, wrapped modulo N */
+static int wrap_index(long mu, int N)
+{
+    long i = (mu + N / 2) % N;
+    if (i < 0)
+        i += N;
+    return (int)i;
+}
+
+static void load(int N, const double* in, cplx* out)
+{
+    for (int i = 0; i < N; ++i)
+        out[i] = in[2 * i] + I * in[2 * i + 1];
+}
+
+static void store(int N, const cplx* in, double* out)
+{
+    for (int i = 0; i < N; ++i) {
+        out[2 * i] = creal(in[i]);
+        out[2 * i + 1] = cimag(in[i]);
+    }
+}
+
+/* Eq. 2 / Eq. 3: direct sum over (beta, gamma) with alpha = mu + beta - gamma. */
+static void fwm_direct(int N, int linear, const cplx* D, cplx* out)
+{
+    const int h = N / 2;
+    for (int mu = -h; mu < N - h; ++mu) {
+        cplx s = 0.0;
+        for (int beta = -h; beta < N - h; ++beta) {
+            const cplx cb = conj(D[beta + h]);
+            for (int gamma = -h; gamma < N - h; ++gamma) {
+                long alpha = (long)mu + beta - gamma;
+                int ia;
+                if (linear) {
+                    if (alpha < -h || alpha >= N - h)
+                        continue;
+                    ia = (int)(alpha + h);
+                } else {
+                    ia = wrap_index(alpha, N);
+                }
+                s += D[ia] * cb * D[gamma + h];
+            }
+        }
+        out[mu + h] = s;
+    }
+}
+
+typedef struct {
+    int N;
+    int linear;
+    const double* kappa;
+    const double* omega;
+    double g0;
+    double kappa_ext;
+    cplx A_in;
+    double sigma;
+} model;
+
+/* F(D) = pump + i g0 FWM(D) */
+static void rhs_nonlinear(const model* m, const cplx* D, cplx* out)
+{
+    fwm_direct(m->N, m->linear, D, out);
+    for (int i = 0; i < m->N; ++i)
+        out[i] *= I * m->g0;
+    out[m->N / 2] += sqrt(m->kappa_ext) * m->A_in;
+}
+
+static cplx lin_coef(const model* m, int i)
+{
+    const double omega0 = m->omega[m->N / 2];
+    return -0.5 * m->kappa[i] + I * (m->omega[i] - omega0 - m->sigma);
+}
+
+/* One RK4IP step (Hult, J. Lightwave Technol. 25, 3770 (2007)) with E = exp(L h/2). */
+static void step_rk4ip(const model* m, double h, cplx* D, cplx* w)
+{
+    const int N = m->N;
+    cplx *E = w, *AI = w + N, *k1 = w + 2 * N, *k2 = w + 3 * N, *k3 = w + 4 * N,
+         *k4 = w + 5 * N, *x = w + 6 * N;
+    for (int i = 0; i < N; ++i)
+        E[i] = cexp(lin_coef(m, i) * (0.5 * h));
+    for (int i = 0; i < N; ++i)
+        AI[i] = E[i] * D[i];
+    rhs_nonlinear(m, D, k1);
+    for (int i = 0; i < N; ++i)
+        k1[i] *= E[i];
+    for (int i = 0; i < N; ++i)
+        x[i] = AI[i] + 0.5 * h * k1[i];
+    rhs_nonlinear(m, x, k2);
+    for (int i = 0; i < N; ++i)
+        x[i] = AI[i] + 0.5 * h * k2[i];
+    rhs_nonlinear(m, x, k3);
+    for (int i = 0; i < N; ++i)
+        x[i] = E[i] * (AI[i] + h * k3[i]);
+    rhs_nonlinear(m, x, k4);
+    for (int i = 0; i < N; ++i)
+        D[i] = E[i] * (AI[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i])) + h / 6.0 * k4[i];
+}
+
+/* Classic RK4 on the full right-hand side L D + F(D). */
+static void full_rhs(const model* m, const cplx* D, cplx* out)
+{
+    rhs_nonlinear(m, D, out);
+    for (int i = 0; i < m->N; ++i)
+        out[i] += lin_coef(m, i) * D[i];
+}
+
+static void step_rk4(const model* m, double h, cplx* D, cplx* w)
+{
+    const int N = m->N;
+    cplx *k1 = w, *k2 = w + N, *k3 = w + 2 * N, *k4 = w + 3 * N, *x = w + 4 * N;
+    full_rhs(m, D, k1);
+    for (int i = 0; i < N; ++i)
+        x[i] = D[i] + 0.5 * h * k1[i];
+    full_rhs(m, x, k2);
+    for (int i = 0; i < N; ++i)
+        x[i] = D[i] + 0.5 * h * k2[i];
+    full_rhs(m, x, k3);
+    for (int i = 0; i < N; ++i)
+        x[i] = D[i] + h * k3[i];
+    full_rhs(m, x, k4);
+    for (int i = 0; i < N; ++i)
+        D[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* Naive transform over the mode number (Eq. 4 without the FFT):
+ *   sign=+1: a_j = sum_mu D_mu exp(+2 pi i j mu / N)          (time samples, j = 0..N-1)
+ *   sign=-1: D_mu = sum_j a_j exp(-2 pi i j mu / N)           (mode amplitudes, centred)
+ * The "time" array is indexed by j = 0..N-1. */
+static void dft_modes_to_time(int N, const cplx* D, cplx* a)
+{
+    for (int j = 0; j < N; ++j) {
+        cplx s = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const long mu = i - N / 2;
+            const long e = ((long)j * mu) % N;
+            s += D[i] * cexp(I * (2.0 * M_PI * (double)e / (double)N));
+        }
+        a[j] = s;
+    }
+}
+
+static void dft_time_to_modes(int N, const cplx* a, cplx* D)
+{
+    for (int i = 0; i < N; ++i) {
+        const long mu = i - N / 2;
+        cplx s = 0.0;
+        for (int j = 0; j < N; ++j) {
+            const long e = ((long)j * mu) % N;
+            s += a[j] * cexp(-I * (2.0 * M_PI * (double)e / (double)N));
+        }
+        D[i] = s;
+    }
+}
+
+/* Exact solution of the linear part dD/dtau = L D + delta_{mu,0} p over a time dt. */
+static void linear_substep(const model* m, double dt, cplx* D)
+{
+    const int N = m->N;
+    const cplx p = sqrt(m->kappa_ext) * m->A_in;
+    for (int i = 0; i < N; ++i) {
+        const cplx L = lin_coef(m, i);
+        const cplx e = cexp(L * dt);
+        D[i] = e * D[i];
+        if (i == N / 2) {
+            if (cabs(L) == 0.0)
+                D[i] += dt * p;
+            else
+                D[i] += (e - 1.0) / L * p;
+        }
+    }
+}
+
+/* Strang split step: linear half step, exact Kerr step in the time domain, linear half step.
+ * With a = (unnormalised) inverse transform of D, the nonlinear flow of the circular CME is
+ * da_j/dtau = i g0 |a_j|^2 a_j, whose exact solution keeps |a_j| and rotates the phase. */
+static void step_strang(const model* m, double h, cplx* D, cplx* w)
+{
+    const int N = m->N;
+    cplx* a = w;
+    linear_substep(m, 0.5 * h, D);
+    dft_modes_to_time(N, D, a);
+    for (int j = 0; j < N; ++j) {
+        const double p2 = creal(a[j]) * creal(a[j]) + cimag(a[j]) * cimag(a[j]);
+        a[j] *= cexp(I * (m->g0 * p2 * h));
+    }
+    dft_time_to_modes(N, a, D);
+    for (int i = 0; i < N; ++i)
+        D[i] /= (double)N;
+    linear_substep(m, 0.5 * h, D);
+}
+
+static int check_model(int N, const double* kappa, const double* omega)
+{
+    if (N < 1 || !kappa || !omega)
+        return ORACLE_EINVAL;
+    return ORACLE_OK;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Exported entry points (plain doubles; complex arrays interleaved re, im).
+ * ------------------------------------------------------------------------------------- */
+
+int oracle_fwm(int N, int linear, const double* D, double* out)
+{
+    if (N < 1 || !D || !out)
+        return ORACLE_EINVAL;
+    cplx* d = malloc(sizeof(cplx) * 2 * N);
+    load(N, D, d);
+    fwm_direct(N, linear, d, d + N);
+    store(N, d + N, out);
+    free(d);
+    return ORACLE_OK;
+}
+
+/* F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D) */
+int oracle_rhs(int N, int linear, double g0, double kappa_ext, double ain_re, double ain_im,
+               const double* D, double* out)
+{
+    if (N < 1 || !D || !out)
+        return ORACLE_EINVAL;
+    model m = {N, linear, NULL, NULL, g0, kappa_ext, ain_re + I * ain_im, 0.0};
+    cplx* d = malloc(sizeof(cplx) * 2 * N);
+    load(N, D, d);
+    rhs_nonlinear(&m, d, d + N);
+    store(N, d + N, out);
+    free(d);
+    return ORACLE_OK;
+}
+
+/* method: 0 = RK4IP, 1 = Strang, 2 = plain RK4.  D (2N doubles) is advanced in place. */
+int oracle_integrate(int method, int N, int linear, const double* kappa, const double* omega,
+                     double g0, double kappa_ext, double ain_re, double ain_im, double sigma,
+                     double h, long nsteps, double* D)
+{
+    if (check_model(N, kappa, omega) || !D || nsteps < 0 || method < 0 || method > 2)
+        return ORACLE_EINVAL;
+    if (method == 1 && linear)
+        return ORACLE_EINVAL;
+    model m = {N, linear, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    cplx* d = malloc(sizeof(cplx) * N);
+    cplx* w = malloc(sizeof(cplx) * 8 * N);
+    load(N, D, d);
+    for (long n = 0; n < nsteps; ++n) {
+        if (method == 0)
+            step_rk4ip(&m, h, d, w);
+        else if (method == 1)
+            step_strang(&m, h, d, w);
+        else
+            step_rk4(&m, h, d, w);
+    }
+    store(N, d, D);
+    free(d);
+    free(w);
+    return ORACLE_OK;
+}
+
+/* Eq. 1 exactly as printed, in the laboratory frame with its explicit phase factors:
+ *   dA_mu/dtau = -kappa_mu/2 A_mu + delta_{mu,0} sqrt(kappa_ext) A_in exp(i sigma tau)
+ *              + i g0 sum_{alpha-beta+gamma=mu} A_alpha conj(A_beta) A_gamma
+ *                      exp(i (omega_alpha - omega_beta + omega_gamma - omega_mu) tau),
+ * integrated with classic RK4 from tau0.  Used to pin the change of frame. */
+static void rhs_eq1(const model* m, double tau, const cplx* A, cplx* out)
+{
+    const int N = m->N, hN = N / 2;
+    for (int mu = -hN; mu < N - hN; ++mu) {
+        cplx s = 0.0;
+        for (int beta = -hN; beta < N - hN; ++beta) {
+            for (int gamma = -hN; gamma < N - hN; ++gamma) {
+                long alpha = (long)mu + beta - gamma;
+                int ia;
+                if (m->linear) {
+                    if (alpha < -hN || alpha >= N - hN)
+                        continue;
+                    ia = (int)(alpha + hN);
+                } else {
+                    ia = wrap_index(alpha, N);
+                }
+                const double ph = m->omega[ia] - m->omega[beta + hN] + m->omega[gamma + hN]
+                                  - m->omega[mu + hN];
+                s += A[ia] * conj(A[beta + hN]) * A[gamma + hN] * cexp(I * ph * tau);
+            }
+        }
+        out[mu + hN] = -0.5 * m->kappa[mu + hN] * A[mu + hN] + I * m->g0 * s;
+    }
+    out[hN] += sqrt(m->kappa_ext) * m->A_in * cexp(I * m->sigma * tau);
+}
+
+int oracle_integrate_eq1(int N, int linear, const double* kappa, const double* omega, double g0,
+                         double kappa_ext, double ain_re, double ain_im, double sigma,
+                         double tau0, double h, long nsteps, double* A)
+{
+    if (check_model(N, kappa, omega) || !A || nsteps < 0)
+        return ORACLE_EINVAL;
+    model m = {N, linear, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    cplx* a = malloc(sizeof(cplx) * 6 * N);
+    cplx *k1 = a + N, *k2 = a + 2 * N, *k3 = a + 3 * N, *k4 = a + 4 * N, *x = a + 5 * N;
+    load(N, A, a);
+    double tau = tau0;
+    for (long n = 0; n < nsteps; ++n) {
+        rhs_eq1(&m, tau, a, k1);
+        for (int i = 0; i < N; ++i)
+            x[i] = a[i] + 0.5 * h * k1[i];
+        rhs_eq1(&m, tau + 0.5 * h, x, k2);
+        for (int i = 0; i < N; ++i)
+            x[i] = a[i] + 0.5 * h * k2[i];
+        rhs_eq1(&m, tau + 0.5 * h, x, k3);
+        for (int i = 0; i < N; ++i)
+            x[i] = a[i] + h * k3[i];
+        rhs_eq1(&m, tau + h, x, k4);
+        for (int i = 0; i < N; ++i)
+            a[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+        tau = tau0 + (double)(n + 1) * h;
+    }
+    store(N, a, A);
+    free(a);
+    return ORACLE_OK;
+}
+
+/* Naive transform over the mode number.  sign=+1: modes -> time; sign=-1: time -> modes. */
+int oracle_dft(int N, int sign, const double* in, double* out)
+{
+    if (N < 1 || !in || !out || (sign != 1 && sign != -1))
+        return ORACLE_EINVAL;
+    cplx* d = malloc(sizeof(cplx) * 2 * N);
+    load(N, in, d);
+    if (sign == 1)
+        dft_modes_to_time(N, d, d + N);
+    else
+        dft_time_to_modes(N, d, d + N);
+    store(N, d + N, out);
+    free(d);
+    return ORACLE_OK;
+}
+
+/* Conserved quantities of the lossless, unpumped system (kappa = 0, A_in = 0):
+ *   out[0] = sum_mu |D_mu|^2
+ *   out[1] = H = sum_mu (omega_mu - omega_0 - sigma) |D_mu|^2 + (g0/2) sum_mu conj(D_mu) FWM_mu(D)
+ * with dD_mu/dtau = i dH/d conj(D_mu). */
+int oracle_invariants(int N, int linear, const double* omega, double g0, double sigma,
+                      const double* D, double* out)
+{
+    if (N < 1 || !omega || !D || !out)
+        return ORACLE_EINVAL;
+    cplx* d = malloc(sizeof(cplx) * 2 * N);
+    load(N, D, d);
+    fwm_direct(N, linear, d, d + N);
+    double norm = 0.0, quad = 0.0;
+    cplx quart = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double p = creal(d[i]) * creal(d[i]) + cimag(d[i]) * cimag(d[i]);
+        norm += p;
+        quad += (omega[i] - omega[N / 2] - sigma) * p;
+        quart += conj(d[i]) * d[N + i];
+    }
+    out[0] = norm;
+    out[1] = quad + 0.5 * g0 * creal(quart);
+    free(d);
+    return ORACLE_OK;
+}
