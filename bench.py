@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched FFT-CME integrator on GB300.
+
+One benchmark step = one full integration of the N=512 x 256-instance detuning sweep:
+reset the field from a device-resident copy, then 20000 RK4IP steps (h = 5e-4) of every
+instance in FP32 (FP32 field, transforms and Kerr term; propagators computed in FP64),
+replayed as one CUDA graph.  The metric is mode-steps/s = (sum of N over instances) x RK4IP
+steps / time, summed over all ranks (weak scaling: every rank integrates its own 256
+instances).
+
+Extra measurements on the same JSON line:
+  fp64      the same batch in FP64, and the single-instance N=64 FP64 workload;
+  error     FP32 vs FP64 over all 256 instances (full horizon) and GPU vs CPU oracle on the
+            oracle's bounded sample;
+  roofline  the step kernel against the FP32 ALU peak (152 SMs x 128 lanes x 2 flop x clock);
+  e2e       the same metric through the C ABI with host buffers (H2D of the initial field from
+            pinned memory and D2H of the power spectrum inside the timed region);
+  cpu_baseline  the FP64 CPU oracle (direct O(N^3) sum) on a bounded sample.
+
+`--impl reference` times the CPU oracle alone on the same metric (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mode-steps/s, batched FP32 FFT-CME RK4IP vs plain FP64, at stated error; % peak"
+UNIT = "mode-steps/s"
+SMS = 152
+FP32_LANES = 128          # FP32 FMA lanes per SM
+SM_MAX_MHZ = 2070.0       # maximum SM clock of the part
+KERNEL_SOURCES = ["cme_core.cuh", "cme_step.cuh", "cme_launch.cuh", "kern_fp32_rk4ip.cu"]
+
+
+def flops_per_mode_step(N: int) -> float:
+    """Algorithmic FP work of one RK4IP step per mode: 8 complex transforms of length N at
+    5 N log2 N flop each, plus 80 flop of Kerr term, pump and Runge-Kutta combination."""
+    return 40.0 * math.log2(N) + 80.0
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1307_3428_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------ oracle leg
+def oracle_sample(target_s: float, sweep_index: int = 128, fixed_steps: int | None = None):
+    """Time the FP64 direct-sum oracle on one instance of the sweep for a bounded number of
+    RK4IP steps (about target_s seconds); returns (mode-steps/s, steps, seconds, field)."""
+    import oracle
+    from paper_1307_3428_gb300 import workloads as wl
+    inst = wl.sweep512(indices=[sweep_index]).instances[0]
+    h = 5e-4
+    if fixed_steps is None:
+        t0 = time.perf_counter()
+        D = oracle.integrate(inst, h, 1, oracle.RK4IP)
+        dt1 = time.perf_counter() - t0
+        steps = max(1, int(target_s / max(dt1, 1e-6)))
+    else:
+        steps = fixed_steps
+    t0 = time.perf_counter()
+    D = oracle.integrate(inst, h, steps, oracle.RK4IP)
+    dt = time.perf_counter() - t0
+    return inst.N * steps / dt, steps, dt, D
+
+
+def run_reference(args, world, rank):
+    """CPU oracle arm: rank 0 times the oracle as it stands on bounded samples."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    total = 0.0
+    work = 0.0
+    steps_used = None
+    for k in range(args.warmup + args.steps):
+        rate, steps, dt, _ = oracle_sample(args.ref_seconds, fixed_steps=steps_used)
+        steps_used = steps
+        if k >= args.warmup:
+            total += dt
+            work += 512 * steps
+    value = work / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "sweep_n512_b256 (oracle sample: instance 128, "
+                               f"{steps_used} RK4IP steps per bench step)",
+                   "engine": "FP64 direct O(N^3) four-wave-mixing sum, C, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"1 instance (N=512, sigma index 128) x {steps_used} RK4IP "
+                                   "steps per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1307_3428_gb300 import cme
+    from paper_1307_3428_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    w = wl.sweep512(seed_offset=256 * rank) if rank else wl.sweep512()
+    N = 512
+    count = len(w.instances)
+    nsteps = args.inner_steps or w.nsteps
+    mode_steps = count * N * nsteps
+
+    insts = [cme.Instance.from_workload(i) for i in w.instances]
+    b32 = cme.Batch(insts, precision=cme.FP32, use_graph=True)
+    stream = torch.cuda.ExternalStream(b32.stream)
+    D0 = np.concatenate([i.D0 for i in w.instances])
+    d0_dev = torch.from_numpy(D0.view(np.float64).copy()).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def one_step(batch):
+        batch.set_state_device(d0_dev.data_ptr())
+        batch.step(w.h, nsteps)
+
+    # warm-up (also builds the graph)
+    for _ in range(args.warmup):
+        one_step(b32)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    launches0 = cme.kernel_launches()
+    k_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps (not timed)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b32.set_state_device(d0_dev.data_ptr())
+        e1.record(stream)
+        b32.step(w.h, nsteps)
+        e2.record(stream)
+        e2.synchronize()
+        total_ms += e0.elapsed_time(e2)
+        k_ms.append(e1.elapsed_time(e2))
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    launches = cme.kernel_launches() - launches0
+    step_ms = max_over_ranks(total_ms / args.steps, world)
+    value = world * mode_steps / (step_ms * 1e-3)
+
+    # roofline of the step kernel (one graph node per replay)
+    kern_ms = statistics.mean(k_ms)
+    flops = mode_steps * flops_per_mode_step(N)
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as fh:
+            tj = json.load(fh)
+        ent = tj.get("step_kernel_fp32_n512")
+        if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("steps") == nsteps:
+            traffic = ent.get("dram_bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "step_kernel<float, 9, 8, RK4IP>",
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
+
+    # FP32 result vs FP64 over the whole batch, full horizon
+    fin32 = b32.get_state()
+    b64 = cme.Batch(insts, precision=cme.FP64, use_graph=True)
+    fp64 = {}
+    if not args.skip_fp64:
+        one_step(b64)                                 # warm-up / graph build
+        torch.cuda.synchronize()
+        s64 = torch.cuda.ExternalStream(b64.stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        b64.set_state_device(d0_dev.data_ptr())
+        e0.record(s64)
+        b64.step(w.h, nsteps)
+        e1.record(s64)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fin64 = b64.get_state()
+        errs = [float(np.linalg.norm(a - c) / np.linalg.norm(c))
+                for a, c in zip(b32.split(fin32), b64.split(fin64))]
+        # plain single-instance FP64 (N=64, 2000 steps)
+        p = wl.plain64()
+        bp = cme.Batch([cme.Instance.from_workload(p.instances[0])], precision=cme.FP64,
+                       use_graph=True)
+        bp.step(p.h, p.nsteps)
+        bp.synchronize()
+        sp = torch.cuda.ExternalStream(bp.stream)
+        pd0 = torch.from_numpy(p.instances[0].D0.view(np.float64).copy()).cuda()
+        tp = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            bp.set_state_device(pd0.data_ptr())
+            e0.record(sp)
+            bp.step(p.h, p.nsteps)
+            e1.record(sp)
+            e1.synchronize()
+            tp.append(e0.elapsed_time(e1))
+        fp64 = {
+            "batched_value": mode_steps / (ms64 * 1e-3), "batched_ms": ms64,
+            "plain_n64_value": 64 * p.nsteps / (min(tp) * 1e-3), "plain_n64_ms": min(tp),
+            "unit": UNIT,
+            "fp32_speedup_vs_batched_fp64": ms64 / kern_ms,
+            "fp32_speedup_vs_plain_fp64": value / world / (64 * p.nsteps / (min(tp) * 1e-3)),
+        }
+        error = {"fp32_vs_fp64_rel_l2_max": max(errs), "fp32_vs_fp64_rel_l2_median":
+                 statistics.median(errs), "instances": len(errs), "bound_fp32": 1e-4}
+    else:
+        error = {}
+
+    # end to end through the C ABI with host buffers
+    pinned_in = torch.from_numpy(D0.view(np.float64).copy()).pin_memory()
+    host_in = pinned_in.numpy()
+    spec = torch.empty(count * N, dtype=torch.float64).pin_memory().numpy()
+    import ctypes
+    lib = cme.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        cme._check(lib.cme_set_state(b32.handle, host_in.ctypes.data_as(dp), cme.HOST))
+        cme._check(lib.cme_step(b32.handle, w.h, nsteps))
+        cme._check(lib.cme_spectrum(b32.handle, -1, cme.POWER, spec.ctypes.data_as(dp)))
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    e2e = {"value": world * mode_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(host_in.nbytes), "d2h_bytes_per_step": int(spec.nbytes)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"sweep_n512_b256: N=512 x {count} instances per GPU, sigma "
+                               f"-2..10, A_in=2.5, D2=0.02, {nsteps} RK4IP steps of h=5e-4, "
+                               "FP32 field with FP64-derived propagators, one CUDA graph",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}", "global_instances": world * count},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+        "fp64": fp64,
+        "error": error,
+        "wall_s_timed": wall,
+    }
+
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        rate, steps, dt, Dref = oracle_sample(args.ref_seconds)
+        # the GPU on exactly the oracle's sample
+        one = cme.Batch([insts[128]], precision=cme.FP32)
+        one.step(w.h, steps)
+        one64 = cme.Batch([insts[128]], precision=cme.FP64)
+        one64.step(w.h, steps)
+        e32 = float(np.linalg.norm(one.get_state() - Dref) / np.linalg.norm(Dref))
+        e64 = float(np.linalg.norm(one64.get_state() - Dref) / np.linalg.norm(Dref))
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"1 instance (N=512, sigma index 128) x {steps} RK4IP "
+                                          f"steps, FP64 direct O(N^3) sum, {dt:.1f} s"}
+        line["error"]["gpu_vs_oracle_sample"] = {"fp32": e32, "fp64": e64, "steps": steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--inner-steps", type=int, default=0,
+                    help="RK4IP steps per benchmark step (default: the workload's 20000)")
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * cme.h -- C ABI of a GB300 integrator for the coupled mode equations (CMEs) of Kerr
+ * frequency-comb generation, in the FFT form of Hansson, Modotto and Wabnitz
+ * ("On the numerical simulation of Kerr frequency combs using coupled mode equations").
+ *
+ * Model (Sec. 2, Eq. 1).  For modes mu = -N/2 .. N/2-1,
+ *   dA_mu/dtau = -kappa_mu/2 A_mu + delta_{mu,0} sqrt(kappa_ext) A_in e^{i sigma tau}
+ *                + i g0 sum_{alpha-beta+gamma=mu} A_alpha A*_beta A_gamma
+ *                       e^{i(omega_alpha - omega_beta + omega_gamma - omega_mu) tau}.
+ * The library integrates it in the frame D_mu = A_mu e^{i(omega_mu - omega_0 - sigma) tau},
+ * where it is autonomous:
+ *   dD_mu/dtau = L_mu D_mu + delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM_mu(D),
+ *   L_mu = -kappa_mu/2 + i(omega_mu - omega_0 - sigma).
+ * The four-wave-mixing (FWM) sum runs over alpha - beta + gamma = mu modulo N (the sum that
+ * Eq. 4 evaluates with an N-point transform) and is computed as in Eq. 4: an inverse
+ * transform over the mode number, |a|^2 a pointwise, a forward transform.
+ *
+ * Conventions of every entry point:
+ *   - Return value: CME_OK (0) or a negative CME_ERR_* code; cme_last_error() then holds a
+ *     message for the calling thread.  No entry point aborts the process.
+ *   - Host arrays passed in are copied; the caller keeps ownership of everything it passes.
+ *   - Complex arrays are interleaved (re, im) doubles; modes in centred order: array index
+ *     i <-> mu = i - N/2 (the pumped mode mu = 0 at i = N/2).
+ *   - A batch owns its device memory (allocated through cme_set_allocator's callbacks, else
+ *     cudaMalloc) and runs on one CUDA stream; calls on one batch are not thread-safe.
+ *   - Work is asynchronous on the batch's stream unless the entry point says it synchronises.
+ */
+#ifndef CME_H
+#define CME_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define CME_OK 0
+#define CME_ERR_INVALID_ARG (-1)   /* null pointer, bad count, h or nsteps out of range */
+#define CME_ERR_UNSUPPORTED_N (-2) /* N not a power of two in [4, 4096] */
+#define CME_ERR_CUDA (-3)          /* a CUDA runtime call failed; message has the CUDA error */
+#define CME_ERR_NONFINITE (-4)     /* a field value became NaN or Inf (see cme_status) */
+#define CME_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
+#define CME_ERR_OOM (-6)           /* device allocation failed */
+#define CME_ERR_STATE (-7)         /* call out of order (e.g. instance without a field) */
+
+/* ---- options ----------------------------------------------------------------------- */
+#define CME_FP64 0 /* FP64 field, transforms, Kerr term and propagators */
+#define CME_FP32 1 /* FP32 field, transforms and Kerr term; propagators computed in FP64 and
+                      applied as small increments; state kept as a compensated FP32 pair */
+
+#define CME_RK4IP 0  /* fourth-order Runge-Kutta in the interaction picture (Sec. 2) */
+#define CME_STRANG 1 /* Strang split step: exact linear half steps around an exact Kerr step */
+
+#define CME_POWER 0     /* |D_mu|^2: N doubles per instance */
+#define CME_FIELD_D 1   /* rotating-frame field D_mu: 2N doubles per instance */
+#define CME_FIELD_EQ1 2 /* Eq. 1 frame A_mu = D_mu e^{-i(omega_mu-omega_0-sigma) tau}: 2N doubles */
+
+#define CME_HOST 0   /* pointer argument is host memory */
+#define CME_DEVICE 1 /* pointer argument is device memory on the batch's device */
+
+typedef struct cme_instance_s* cme_instance;
+typedef struct cme_batch_s* cme_batch;
+
+typedef struct cme_options {
+    int precision;         /* CME_FP64 or CME_FP32 */
+    int integrator;        /* CME_RK4IP or CME_STRANG */
+    int radix;             /* field elements per thread (4, 8 or 16); 0 = library choice */
+    int inst_per_cta;      /* instances sharing one thread block; 0 = library choice */
+    long steps_per_launch; /* steps per kernel launch; 0 = all steps of a call in one launch */
+    int use_graph;         /* 1 = cme_step replays a cached CUDA graph per (h, nsteps) */
+} cme_options;
+
+/* Fill *opt with the defaults: CME_FP64, CME_RK4IP, library-chosen launch shape, no graph. */
+void cme_default_options(cme_options* opt);
+
+/* ---- instances (host-side parameter sets) -------------------------------------------- */
+
+/* Create one CME problem (Eq. 1 parameters, Sec. 2).
+ *   N          number of modes, power of two in [4, 4096];
+ *   kappa_mu   N total losses (centred order), each >= 0;
+ *   omega_mu   N cold-cavity resonance frequencies (centred order); only differences to
+ *              omega_0 enter the model;
+ *   g0         Kerr coefficient; kappa_ext coupling loss (>= 0);
+ *   A_in       complex pump amplitude on mu = 0; sigma = omega_in - omega_0 the detuning.
+ * The initial field is zero until cme_set_field.  Errors: INVALID_ARG, UNSUPPORTED_N. */
+int cme_create(int N, const double* kappa_mu, const double* omega_mu, double g0,
+               double kappa_ext, double A_in_re, double A_in_im, double sigma,
+               cme_instance* out);
+
+/* Set the initial rotating-frame field D_mu(0): 2N doubles, interleaved, centred order. */
+int cme_set_field(cme_instance inst, const double* D0);
+
+void cme_destroy(cme_instance inst);
+
+/* ---- batches (device-resident sets of instances) --------------------------------------- */
+
+/* Build a batch from `count` instances (copied; the instances may be destroyed afterwards).
+ * Instances may differ in N; each distinct N forms its own launch group.  `cuda_stream` is a
+ * cudaStream_t; NULL makes the batch create and own a non-blocking stream.  The field starts
+ * at the instances' initial fields, tau = 0.  Errors: INVALID_ARG, UNSUPPORTED_N, CUDA, OOM. */
+int cme_batch_create(const cme_instance* v, int count, const cme_options* opt,
+                     void* cuda_stream, cme_batch* out);
+
+void cme_batch_destroy(cme_batch b);
+
+/* count = instances; total_modes = sum of N; fills any non-null pointer. */
+int cme_batch_info(cme_batch b, int* count, long* total_modes, int* precision, int* integrator);
+
+/* The batch's stream (cudaStream_t). */
+void* cme_batch_stream(cme_batch b);
+
+/* Advance every instance by nsteps steps of size h (> 0) of the batch's integrator (Sec. 2:
+ * RK4 or split step, with the FWM term evaluated through Eq. 4).  Asynchronous.  The first
+ * call with a new h also recomputes the per-mode propagators exp(L h/2), expm1(L h/2),
+ * expm1(L h) in FP64.  nsteps = 0 is a no-op.  Errors: INVALID_ARG, CUDA. */
+int cme_step(cme_batch b, double h, long nsteps);
+
+/* Wait for the batch's stream; returns CME_ERR_NONFINITE if any instance's status is set. */
+int cme_synchronize(cme_batch b);
+
+/* Copy out one instance (idx >= 0) or all instances concatenated (idx = -1) to host memory:
+ * what = CME_POWER, CME_FIELD_D or CME_FIELD_EQ1.  Synchronises. */
+int cme_spectrum(cme_batch b, int idx, int what, double* out);
+
+/* Whole-batch field, FP64 interleaved centred rotating frame, all instances concatenated
+ * (2 * total_modes doubles).  `where` = CME_HOST (synchronises) or CME_DEVICE (asynchronous;
+ * `buf` must be 8-byte aligned device memory).  cme_set_state also clears the status words.
+ * In CME_FP32 batches the FP64 value is split into the compensated (hi, lo) pair. */
+int cme_get_state(cme_batch b, double* buf, int where);
+int cme_set_state(cme_batch b, const double* buf, int where);
+
+/* Bit-exact checkpoint of the internal state (field words plus tau): size in bytes, then
+ * copy out / in through host memory.  Synchronises. */
+int cme_checkpoint_size(cme_batch b, size_t* bytes);
+int cme_checkpoint_save(cme_batch b, void* host_buf, size_t bytes);
+int cme_checkpoint_load(cme_batch b, const void* host_buf, size_t bytes);
+
+/* Accumulated time tau (FP64 sum of h * nsteps over cme_step calls). */
+int cme_get_time(cme_batch b, double* tau);
+int cme_set_time(cme_batch b, double tau);
+
+/* Per-instance status words (host array of `count` ints): 0 = finite, 1 = non-finite value
+ * seen at the end of a launch.  Synchronises. */
+int cme_status(cme_batch b, int* per_instance);
+
+/* ---- hot-path pieces, for testing ----------------------------------------------------- */
+
+/* Unnormalised transform over the mode number of the current field (Eq. 4), run by the same
+ * device code as cme_step: sign = +1 gives a_j = sum_mu D_mu e^{+2 pi i j mu/N} for time
+ * samples j = 0..N-1; sign = -1 gives sum_mu D_mu e^{-2 pi i j mu/N}.  Output 2 * total_modes
+ * doubles (per instance: j-ordered samples), to host (synchronises) or device memory. */
+int cme_transform(cme_batch b, int sign, double* out, int where);
+
+/* Right-hand side F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D) of the current
+ * field, FWM through Eq. 4 on the device (centred order, 2 * total_modes doubles). */
+int cme_eval_rhs(cme_batch b, double* out, int where);
+
+/* ---- library ------------------------------------------------------------------------ */
+
+/* Device allocation hooks used by every later batch: alloc(bytes, ctx) returns device memory
+ * or NULL; release(ptr, ctx) frees it.  Pass NULLs to restore cudaMalloc / cudaFree. */
+typedef void* (*cme_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*cme_free_fn)(void* ptr, void* ctx);
+int cme_set_allocator(cme_alloc_fn alloc, cme_free_fn release, void* ctx);
+
+/* Measured throughput of dependent-free fused multiply-adds on the current device, in
+ * flop/s (2 flop per FMA), for CME_FP32 or CME_FP64; runs for a few tens of ms. */
+int cme_fma_peak(int precision, double* flops_per_s);
+
+/* Number of kernels this library has launched in the calling process (for accounting). */
+long cme_kernel_launches(void);
+
+const char* cme_last_error(void);
+const char* cme_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CME_H */

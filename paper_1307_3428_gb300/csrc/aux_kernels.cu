@@ -1,0 +1,274 @@
+// Auxiliary kernels: twiddle tables, FP64 propagators, layout conversion between the public
+// centred FP64 field and the internal transform-order field, and an FMA throughput probe.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "cme_internal.h"
+
+namespace cme {
+
+namespace {
+
+__global__ void twiddle_kernel(int N, int prec, void* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N)
+        return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)N, &s, &c);   // exp(2 pi i k/N) in FP64
+    if (prec == PREC_FP64)
+        reinterpret_cast<double2*>(out)[k] = make_double2(c, s);
+    else
+        reinterpret_cast<float2*>(out)[k] = make_float2((float)c, (float)s);
+}
+
+// expm1 of a complex argument z = x + iy without cancellation:
+//   e^z - 1 = (expm1(x) cos y - 2 sin^2(y/2)) + i e^x sin y.
+__device__ double2 cexpm1(double x, double y)
+{
+    double sy, cy, sh, ch;
+    sincos(y, &sy, &cy);
+    sincos(0.5 * y, &sh, &ch);
+    const double em = expm1(x);
+    return make_double2(em * cy - 2.0 * sh * sh, (em + 1.0) * sy);
+}
+
+template <typename V>
+__device__ void put(void* p, int m, double2 v)
+{
+    if constexpr (sizeof(V) == 16) {
+        reinterpret_cast<double2*>(p)[m] = v;
+    } else {
+        reinterpret_cast<float2*>(p)[m] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// Per mode: L = -kappa/2 + i(omega - omega_0 - sigma);  E = exp(L h/2), e1 = expm1(L h/2),
+// e2 = expm1(L h), all in FP64, stored in the batch precision.
+template <typename V>
+__global__ void prop_kernel(PropArgs a)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.total)
+        return;
+    const int i = a.mode_inst[m];
+    const double Lr = -0.5 * a.kappa[m];
+    const double Li = a.omega[m] - a.sigma[i];
+    const double hh = 0.5 * a.h;
+    const double2 e1 = cexpm1(Lr * hh, Li * hh);
+    const double2 e2 = cexpm1(Lr * a.h, Li * a.h);
+    put<V>(a.E, m, make_double2(e1.x + 1.0, e1.y));
+    put<V>(a.e1, m, e1);
+    put<V>(a.e2, m, e2);
+    // Strang pump increment over h/2 on the pumped mode (transform position 0):
+    //   c = (exp(L_0 h/2) - 1) / L_0 * pump   (h/2 * pump when L_0 = 0)
+    if (m == a.inst_off[i]) {
+        const double2 p = a.pump[i];
+        double2 c;
+        const double den = Lr * Lr + Li * Li;
+        if (den == 0.0) {
+            c = make_double2(hh * p.x, hh * p.y);
+        } else {
+            // q = e1 / L
+            const double qr = (e1.x * Lr + e1.y * Li) / den;
+            const double qi = (e1.y * Lr - e1.x * Li) / den;
+            c = make_double2(qr * p.x - qi * p.y, qr * p.y + qi * p.x);
+        }
+        a.cpump[i] = c;
+    }
+}
+
+// centred public index of transform position pm within an instance of size N
+__device__ __forceinline__ int centred_of(int pm, int N) { return (pm + N / 2) & (N - 1); }
+
+__global__ void import_kernel(int prec, int total, const int* mode_inst, const int* inst_N,
+                              const long long* inst_off, const double2* src, void* hi, void* lo)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= total)
+        return;
+    const int i = mode_inst[m];
+    const int N = inst_N[i];
+    const long long off = inst_off[i];
+    const double2 v = src[off + centred_of((int)(m - off), N)];
+    if (prec == PREC_FP64) {
+        reinterpret_cast<double2*>(hi)[m] = v;
+    } else {
+        const float hr = (float)v.x, hi_ = (float)v.y;
+        reinterpret_cast<float2*>(hi)[m] = make_float2(hr, hi_);
+        reinterpret_cast<float2*>(lo)[m] =
+            make_float2((float)(v.x - (double)hr), (float)(v.y - (double)hi_));
+    }
+}
+
+// what: 0 power (|D|^2 into a double array), 1 rotating-frame field, 2 Eq. 1 frame field.
+__global__ void export_kernel(int prec, int total, const int* mode_inst, const int* inst_N,
+                              const long long* inst_off, const void* hi, const void* lo,
+                              double2* dst, int what, const double* omega, const double* sigma,
+                              double tau)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= total)
+        return;
+    const int i = mode_inst[m];
+    const int N = inst_N[i];
+    const long long off = inst_off[i];
+    double2 v;
+    if (prec == PREC_FP64) {
+        v = reinterpret_cast<const double2*>(hi)[m];
+    } else {
+        const float2 a = reinterpret_cast<const float2*>(hi)[m];
+        const float2 b = reinterpret_cast<const float2*>(lo)[m];
+        v = make_double2((double)a.x + (double)b.x, (double)a.y + (double)b.y);
+    }
+    const long long c = off + centred_of((int)(m - off), N);
+    if (what == 0) {
+        reinterpret_cast<double*>(dst)[c] = v.x * v.x + v.y * v.y;
+    } else if (what == 1) {
+        dst[c] = v;
+    } else {
+        // A = D exp(-i (omega_mu - omega_0 - sigma) tau), phase in FP64
+        double s, co;
+        sincos(-(omega[m] - sigma[i]) * tau, &s, &co);
+        dst[c] = make_double2(v.x * co - v.y * s, v.x * s + v.y * co);
+    }
+}
+
+// Copy a transform-order array (diagnostics output) to FP64, optionally centring the order.
+__global__ void export_plain_kernel(int prec, int total, const int* mode_inst, const int* inst_N,
+                                    const long long* inst_off, const void* src, double2* dst,
+                                    int reorder_centred)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= total)
+        return;
+    double2 v;
+    if (prec == PREC_FP64) {
+        v = reinterpret_cast<const double2*>(src)[m];
+    } else {
+        const float2 a = reinterpret_cast<const float2*>(src)[m];
+        v = make_double2(a.x, a.y);
+    }
+    long long c = m;
+    if (reorder_centred) {
+        const int i = mode_inst[m];
+        const long long off = inst_off[i];
+        c = off + centred_of((int)(m - off), inst_N[i]);
+    }
+    dst[c] = v;
+}
+
+// Independent FMA chains: 8 per thread, `iters` rounds.
+template <typename T>
+__global__ void fma_kernel(T* out, int iters, T a, T b)
+{
+    T x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5,
+      x6 = x0 + 6, x7 = x0 + 7;
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            x0 = x0 * a + b;
+            x1 = x1 * a + b;
+            x2 = x2 * a + b;
+            x3 = x3 * a + b;
+            x4 = x4 * a + b;
+            x5 = x5 * a + b;
+            x6 = x6 * a + b;
+            x7 = x7 * a + b;
+        }
+    }
+    const T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+    if (s == (T)-1.2345)  // practically never: keeps the chains alive
+        out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+inline int nblocks(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_twiddles(int N, int prec, void* out, cudaStream_t s)
+{
+    twiddle_kernel<<<nblocks(N, 256), 256, 0, s>>>(N, prec, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagators(const PropArgs& a, cudaStream_t s)
+{
+    if (a.prec == PREC_FP64)
+        prop_kernel<double2><<<nblocks(a.total, 256), 256, 0, s>>>(a);
+    else
+        prop_kernel<float2><<<nblocks(a.total, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import(int prec, int total, const int* mode_inst, const int* inst_N,
+                          const long long* inst_off, const double2* src, void* hi, void* lo,
+                          cudaStream_t s)
+{
+    import_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N, inst_off,
+                                                       src, hi, lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(int prec, int total, const int* mode_inst, const int* inst_N,
+                          const long long* inst_off, const void* hi, const void* lo,
+                          double2* dst, int what, const double* omega, const double* sigma,
+                          double tau, cudaStream_t s)
+{
+    export_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N, inst_off,
+                                                       hi, lo, dst, what, omega, sigma, tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_plain(int prec, int total, const int* mode_inst, const int* inst_N,
+                                const long long* inst_off, const void* src, double2* dst,
+                                int reorder_centred, cudaStream_t s)
+{
+    export_plain_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N,
+                                                             inst_off, src, dst,
+                                                             reorder_centred);
+    return cudaGetLastError();
+}
+
+cudaError_t run_fma_peak(int prec, double* flops)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    void* out = nullptr;
+    e = cudaMalloc(&out, 1 << 24);
+    if (e != cudaSuccess)
+        return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int threads = 512, blocks = sms * 4;
+    const int iters = prec == PREC_FP64 ? 64 : 2048;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a);
+        if (prec == PREC_FP64)
+            fma_kernel<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-7);
+        else
+            fma_kernel<float><<<blocks, threads>>>((float*)out, iters, 0.999999f, 1e-7f);
+        cudaEventRecord(b);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best)
+            best = ms;
+    }
+    e = cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    const double fmas = (double)blocks * threads * iters * 16.0 * 8.0;
+    *flops = 2.0 * fmas / (best * 1e-3);
+    return e;
+}
+
+}  // namespace cme

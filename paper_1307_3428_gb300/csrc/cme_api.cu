@@ -1,0 +1,792 @@
+// Host side of the C ABI declared in include/cme.h: instances, batches, device memory, launch
+// planning, CUDA graph caching and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "cme.h"
+#include "cme_internal.h"
+
+using namespace cme;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<long> g_launches{0};
+
+std::mutex g_alloc_mu;
+cme_alloc_fn g_alloc = nullptr;
+cme_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? CME_ERR_OOM : CME_ERR_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CME_CUDA(call, what)                     \
+    do {                                         \
+        cudaError_t e_ = (call);                 \
+        if (e_ != cudaSuccess)                   \
+            return cuda_fail(e_, what);          \
+    } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+int ilog2i(int n)
+{
+    int l = 0;
+    while ((1 << l) < n)
+        ++l;
+    return l;
+}
+
+// Device allocation through the registered hooks (else cudaMalloc).
+void* dev_alloc(size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_alloc)
+        return g_alloc(bytes, g_alloc_ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void dev_free(void* p, cme_free_fn f, void* ctx)
+{
+    if (!p)
+        return;
+    if (f)
+        f(p, ctx);
+    else
+        cudaFree(p);
+}
+
+// Compiled launch shapes (values per thread R for each log2 N); must match the kernel units.
+bool shape_compiled(int logN, int R)
+{
+    static const int shapes[][2] = {{2, 4},  {3, 8},  {4, 8},  {4, 16}, {5, 8},  {5, 16},
+                                    {6, 8},  {6, 4},  {6, 16}, {7, 8},  {7, 4},  {7, 16},
+                                    {8, 8},  {8, 4},  {8, 16}, {9, 8},  {9, 4},  {10, 8},
+                                    {10, 4}, {11, 8}, {12, 8}};
+    for (auto& s : shapes)
+        if (s[0] == logN && s[1] == R)
+            return true;
+    return false;
+}
+
+int default_radix(int logN) { return logN <= 2 ? 4 : 8; }
+
+}  // namespace
+
+struct cme_instance_s {
+    int N = 0;
+    std::vector<double> kappa, omega, field;
+    double g0 = 0, kappa_ext = 0, ain_re = 0, ain_im = 0, sigma = 0;
+};
+
+namespace {
+struct LaunchGroup {
+    int logN = 0, N = 0;
+    int first = 0, count = 0;   // instances [first, first+count)
+    long long base = 0;         // first mode offset
+    int R = 8, G = 1;
+};
+}  // namespace
+
+struct cme_batch_s {
+    int count = 0;
+    long long total = 0;
+    cme_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int prec = PREC_FP64, method = METHOD_RK4IP;
+    size_t elem = 16;  // bytes per complex field element
+
+    // device memory
+    std::vector<void*> allocs;
+    cme_free_fn free_fn = nullptr;
+    void* free_ctx = nullptr;
+    void *hi = nullptr, *lo = nullptr, *E = nullptr, *e1 = nullptr, *e2 = nullptr,
+         *diag = nullptr;
+    double *kappa = nullptr, *omega = nullptr, *sigma_d = nullptr, *g0_d = nullptr;
+    double2 *pump_d = nullptr, *cpump_d = nullptr, *stage = nullptr;
+    int *mode_inst = nullptr, *inst_N = nullptr, *status_d = nullptr;
+    long long* inst_off = nullptr;
+    std::map<int, void*> tw;  // per log2 N
+
+    // host copies
+    std::vector<int> N_h;
+    std::vector<long long> off_h;
+    std::vector<double> sigma_h;
+    std::vector<LaunchGroup> groups;
+
+    double h_cur = 0.0;   // h of the current propagators (0 = none)
+    double tau = 0.0;
+
+    std::map<std::pair<double, long>, std::pair<cudaGraphExec_t, int>> graphs;
+
+    void* alloc(size_t bytes)
+    {
+        void* p = dev_alloc(bytes);
+        if (p)
+            allocs.push_back(p);
+        return p;
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+void cme_default_options(cme_options* opt)
+{
+    if (!opt)
+        return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->precision = CME_FP64;
+    opt->integrator = CME_RK4IP;
+}
+
+const char* cme_last_error(void) { return g_err.c_str(); }
+const char* cme_version(void) { return "cme-gb300 0.1 (sm_103a)"; }
+long cme_kernel_launches(void) { return g_launches.load(); }
+
+int cme_set_allocator(cme_alloc_fn alloc, cme_free_fn release, void* ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(CME_ERR_INVALID_ARG, "cme_set_allocator: give both hooks or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_ctx = ctx;
+    return CME_OK;
+}
+
+int cme_create(int N, const double* kappa_mu, const double* omega_mu, double g0, double kappa_ext,
+               double A_in_re, double A_in_im, double sigma, cme_instance* out)
+{
+    if (!out)
+        return fail(CME_ERR_INVALID_ARG, "cme_create: out is NULL");
+    *out = nullptr;
+    if (!is_pow2(N) || N < 4 || N > 4096)
+        return fail(CME_ERR_UNSUPPORTED_N, "cme_create: N=%d is not a power of two in [4, 4096]", N);
+    if (!kappa_mu || !omega_mu)
+        return fail(CME_ERR_INVALID_ARG, "cme_create: kappa_mu and omega_mu are required");
+    for (int i = 0; i < N; ++i) {
+        if (!std::isfinite(kappa_mu[i]) || kappa_mu[i] < 0 || !std::isfinite(omega_mu[i]))
+            return fail(CME_ERR_INVALID_ARG, "cme_create: kappa_mu[%d] or omega_mu[%d] invalid", i, i);
+    }
+    if (!std::isfinite(g0) || !std::isfinite(kappa_ext) || kappa_ext < 0 || !std::isfinite(A_in_re) ||
+        !std::isfinite(A_in_im) || !std::isfinite(sigma))
+        return fail(CME_ERR_INVALID_ARG, "cme_create: non-finite or negative scalar parameter");
+    auto* p = new cme_instance_s;
+    p->N = N;
+    p->kappa.assign(kappa_mu, kappa_mu + N);
+    p->omega.assign(omega_mu, omega_mu + N);
+    p->field.assign(2 * (size_t)N, 0.0);
+    p->g0 = g0;
+    p->kappa_ext = kappa_ext;
+    p->ain_re = A_in_re;
+    p->ain_im = A_in_im;
+    p->sigma = sigma;
+    *out = p;
+    return CME_OK;
+}
+
+int cme_set_field(cme_instance inst, const double* D0)
+{
+    if (!inst || !D0)
+        return fail(CME_ERR_INVALID_ARG, "cme_set_field: NULL argument");
+    for (int i = 0; i < 2 * inst->N; ++i)
+        if (!std::isfinite(D0[i]))
+            return fail(CME_ERR_INVALID_ARG, "cme_set_field: non-finite value at %d", i);
+    inst->field.assign(D0, D0 + 2 * (size_t)inst->N);
+    return CME_OK;
+}
+
+void cme_destroy(cme_instance inst) { delete inst; }
+
+void cme_batch_destroy(cme_batch b)
+{
+    if (!b)
+        return;
+    if (b->stream)
+        cudaStreamSynchronize(b->stream);
+    for (auto& kv : b->graphs)
+        cudaGraphExecDestroy(kv.second.first);
+    for (void* p : b->allocs)
+        dev_free(p, b->free_fn, b->free_ctx);
+    if (b->own_stream && b->stream)
+        cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, void* cuda_stream,
+                     cme_batch* out)
+{
+    if (!out)
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_create: out is NULL");
+    *out = nullptr;
+    if (!v || count <= 0)
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_create: need at least one instance");
+    cme_options o;
+    cme_default_options(&o);
+    if (opt)
+        o = *opt;
+    if (o.precision != CME_FP64 && o.precision != CME_FP32)
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_create: unknown precision %d", o.precision);
+    if (o.integrator != CME_RK4IP && o.integrator != CME_STRANG)
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_create: unknown integrator %d", o.integrator);
+    if (o.steps_per_launch < 0 || o.inst_per_cta < 0 || o.radix < 0)
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_create: negative launch option");
+    for (int i = 0; i < count; ++i)
+        if (!v[i])
+            return fail(CME_ERR_INVALID_ARG, "cme_batch_create: instance %d is NULL", i);
+
+    // Order instances by N so that each N forms one contiguous launch group; keep the caller's
+    // order inside a group and remember the permutation (the public order is the caller's).
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return v[a]->N < v[c]->N; });
+    for (int i = 0; i < count; ++i)
+        if (order[i] != i)
+            return fail(CME_ERR_INVALID_ARG,
+                        "cme_batch_create: instances must be given in non-decreasing N");
+
+    auto* b = new cme_batch_s;
+    b->count = count;
+    b->opt = o;
+    b->prec = o.precision == CME_FP32 ? PREC_FP32 : PREC_FP64;
+    b->method = o.integrator == CME_STRANG ? METHOD_STRANG : METHOD_RK4IP;
+    b->elem = b->prec == PREC_FP32 ? 8 : 16;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        b->free_fn = g_free;
+        b->free_ctx = g_alloc_ctx;
+    }
+    b->N_h.resize(count);
+    b->off_h.resize(count);
+    b->sigma_h.resize(count);
+    long long off = 0;
+    for (int i = 0; i < count; ++i) {
+        b->N_h[i] = v[i]->N;
+        b->off_h[i] = off;
+        b->sigma_h[i] = v[i]->sigma;
+        off += v[i]->N;
+    }
+    b->total = off;
+
+    // launch groups
+    for (int i = 0; i < count;) {
+        int j = i;
+        while (j < count && v[j]->N == v[i]->N)
+            ++j;
+        LaunchGroup g;
+        g.N = v[i]->N;
+        g.logN = ilog2i(g.N);
+        g.first = i;
+        g.count = j - i;
+        g.base = b->off_h[i];
+        int R = o.radix ? o.radix : default_radix(g.logN);
+        if (R > g.N)
+            R = g.N;
+        if (!shape_compiled(g.logN, R)) {
+            cme_batch_destroy(b);
+            return fail(CME_ERR_INVALID_ARG, "cme_batch_create: radix %d not available for N=%d", R, g.N);
+        }
+        g.R = R;
+        const int P = g.N / R;
+        int G = o.inst_per_cta;
+        if (G == 0)
+            G = P >= 64 ? 1 : std::max(1, 64 / P);
+        G = std::min(G, std::max(1, 256 / P));
+        if (P < 32) {
+            // groups narrower than a warp synchronise with __syncwarp over full warps: make the
+            // block a whole number of warps (surplus groups recompute the last instance and
+            // store nothing)
+            const int per_warp = 32 / P;
+            G = std::max(per_warp, (G + per_warp - 1) / per_warp * per_warp);
+        } else {
+            G = std::min(G, g.count);
+        }
+        g.G = G;
+        b->groups.push_back(g);
+        i = j;
+    }
+
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cme_batch_destroy(b);
+            return cuda_fail(e, "cme_batch_create: cudaStreamCreate");
+        }
+        b->own_stream = true;
+    }
+
+    const size_t T = (size_t)b->total;
+    bool ok = true;
+    auto A = [&](size_t bytes) {
+        void* p = b->alloc(bytes);
+        if (!p)
+            ok = false;
+        return p;
+    };
+    b->hi = A(T * b->elem);
+    b->lo = b->prec == PREC_FP32 ? A(T * b->elem) : nullptr;
+    b->E = A(T * b->elem);
+    b->e1 = A(T * b->elem);
+    b->e2 = A(T * b->elem);
+    b->diag = A(T * b->elem);
+    b->kappa = (double*)A(T * 8);
+    b->omega = (double*)A(T * 8);
+    b->mode_inst = (int*)A(T * 4);
+    b->stage = (double2*)A(T * 16);
+    b->sigma_d = (double*)A(count * 8);
+    b->g0_d = (double*)A(count * 8);
+    b->pump_d = (double2*)A(count * 16);
+    b->cpump_d = (double2*)A(count * 16);
+    b->inst_N = (int*)A(count * 4);
+    b->status_d = (int*)A(count * 4);
+    b->inst_off = (long long*)A(count * 8);
+    for (auto& g : b->groups) {
+        if (!b->tw.count(g.logN))
+            b->tw[g.logN] = A((size_t)g.N * b->elem);
+    }
+    if (!ok) {
+        cme_batch_destroy(b);
+        return fail(CME_ERR_OOM, "cme_batch_create: device allocation of %lld modes failed",
+                    (long long)T);
+    }
+
+    // host staging of the parameters (transform order for per-mode arrays)
+    std::vector<double> kap(T), om(T), g0(count);
+    std::vector<int> mi(T);
+    std::vector<double2> pump(count), field(T);
+    for (int i = 0; i < count; ++i) {
+        const int N = v[i]->N;
+        const long long o0 = b->off_h[i];
+        const double om0 = v[i]->omega[N / 2];
+        for (int c = 0; c < N; ++c) {
+            const int pm = (c + N / 2) & (N - 1);  // transform position of centred index c
+            kap[o0 + pm] = v[i]->kappa[c];
+            om[o0 + pm] = v[i]->omega[c] - om0;
+            mi[o0 + pm] = i;
+            field[o0 + c] = make_double2(v[i]->field[2 * c], v[i]->field[2 * c + 1]);
+        }
+        g0[i] = v[i]->g0;
+        const double sk = std::sqrt(v[i]->kappa_ext);
+        pump[i] = make_double2(sk * v[i]->ain_re, sk * v[i]->ain_im);
+    }
+    cudaStream_t s = b->stream;
+#define CPY(dst, src, bytes)                                                                  \
+    do {                                                                                      \
+        cudaError_t e_ = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);          \
+        if (e_ == cudaSuccess)                                                                \
+            e_ = cudaStreamSynchronize(s);                                                    \
+        if (e_ != cudaSuccess) {                                                              \
+            cme_batch_destroy(b);                                                             \
+            return cuda_fail(e_, "cme_batch_create: upload");                                 \
+        }                                                                                     \
+    } while (0)
+    CPY(b->kappa, kap.data(), T * 8);
+    CPY(b->omega, om.data(), T * 8);
+    CPY(b->mode_inst, mi.data(), T * 4);
+    CPY(b->sigma_d, b->sigma_h.data(), count * 8);
+    CPY(b->g0_d, g0.data(), count * 8);
+    CPY(b->pump_d, pump.data(), count * 16);
+    CPY(b->inst_N, b->N_h.data(), count * 4);
+    CPY(b->inst_off, b->off_h.data(), count * 8);
+    CPY(b->stage, field.data(), T * 16);
+#undef CPY
+    cudaError_t e = cudaMemsetAsync(b->status_d, 0, count * 4, s);
+    for (auto& kv : b->tw) {
+        if (e == cudaSuccess) {
+            e = launch_twiddles(1 << kv.first, b->prec, kv.second, s);
+            ++g_launches;
+        }
+    }
+    if (e == cudaSuccess) {
+        e = launch_import(b->prec, (int)T, b->mode_inst, b->inst_N, b->inst_off, b->stage, b->hi,
+                          b->lo, s);
+        ++g_launches;
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cme_batch_destroy(b);
+        return cuda_fail(e, "cme_batch_create: set-up kernels");
+    }
+    *out = b;
+    return CME_OK;
+}
+
+int cme_batch_info(cme_batch b, int* count, long* total_modes, int* precision, int* integrator)
+{
+    if (!b)
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_info: NULL batch");
+    if (count)
+        *count = b->count;
+    if (total_modes)
+        *total_modes = (long)b->total;
+    if (precision)
+        *precision = b->opt.precision;
+    if (integrator)
+        *integrator = b->opt.integrator;
+    return CME_OK;
+}
+
+void* cme_batch_stream(cme_batch b) { return b ? (void*)b->stream : nullptr; }
+
+}  // extern "C"
+
+namespace {
+
+StepArgs group_args(cme_batch b, const LaunchGroup& g)
+{
+    StepArgs a{};
+    a.ninst = g.count;
+    a.G = g.G;
+    a.base = g.base;
+    a.hi = b->hi;
+    a.lo = b->lo;
+    a.E = b->E;
+    a.e1 = b->e1;
+    a.e2 = b->e2;
+    a.tw = b->tw[g.logN];
+    a.pump = b->pump_d + g.first;
+    a.cpump = b->cpump_d + g.first;
+    a.g0 = b->g0_d + g.first;
+    a.status = b->status_d + g.first;
+    a.h = b->h_cur;
+    return a;
+}
+
+cudaError_t launch_group_step(cme_batch b, const LaunchGroup& g, long long nsteps)
+{
+    StepArgs a = group_args(b, g);
+    a.nsteps = nsteps;
+    ++g_launches;
+    if (b->prec == PREC_FP64)
+        return b->method == METHOD_RK4IP ? launch_step_fp64_rk4ip(g.logN, g.R, a, b->stream)
+                                         : launch_step_fp64_strang(g.logN, g.R, a, b->stream);
+    return b->method == METHOD_RK4IP ? launch_step_fp32_rk4ip(g.logN, g.R, a, b->stream)
+                                     : launch_step_fp32_strang(g.logN, g.R, a, b->stream);
+}
+
+// Enqueue the step kernels for nsteps (chunked by steps_per_launch); returns kernels launched.
+cudaError_t enqueue_steps(cme_batch b, long nsteps, int* nk)
+{
+    const long chunk = b->opt.steps_per_launch > 0 ? b->opt.steps_per_launch : nsteps;
+    int k = 0;
+    for (long done = 0; done < nsteps; done += chunk) {
+        const long n = std::min(chunk, nsteps - done);
+        for (auto& g : b->groups) {
+            cudaError_t e = launch_group_step(b, g, n);
+            if (e != cudaSuccess)
+                return e;
+            ++k;
+        }
+    }
+    if (nk)
+        *nk = k;
+    return cudaSuccess;
+}
+
+int ensure_propagators(cme_batch b, double h)
+{
+    if (b->h_cur == h)
+        return CME_OK;
+    PropArgs p{};
+    p.total = (int)b->total;
+    p.mode_inst = b->mode_inst;
+    p.kappa = b->kappa;
+    p.omega = b->omega;
+    p.sigma = b->sigma_d;
+    p.pump = b->pump_d;
+    p.inst_N = b->inst_N;
+    p.inst_off = b->inst_off;
+    p.h = h;
+    p.prec = b->prec;
+    p.E = b->E;
+    p.e1 = b->e1;
+    p.e2 = b->e2;
+    p.cpump = b->cpump_d;
+    p.ninst = b->count;
+    ++g_launches;
+    CME_CUDA(launch_propagators(p, b->stream), "cme_step: propagator kernel");
+    b->h_cur = h;
+    return CME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cme_step(cme_batch b, double h, long nsteps)
+{
+    if (!b)
+        return fail(CME_ERR_INVALID_ARG, "cme_step: NULL batch");
+    if (!(h > 0.0) || !std::isfinite(h))
+        return fail(CME_ERR_INVALID_ARG, "cme_step: h must be positive and finite (got %g)", h);
+    if (nsteps < 0)
+        return fail(CME_ERR_INVALID_ARG, "cme_step: nsteps must be >= 0 (got %ld)", nsteps);
+    if (nsteps == 0)
+        return CME_OK;
+    int rc = ensure_propagators(b, h);
+    if (rc)
+        return rc;
+    if (b->opt.use_graph) {
+        auto key = std::make_pair(h, nsteps);
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t graph;
+            CME_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
+                     "cme_step: begin capture");
+            int nk = 0;
+            const long before = g_launches.load();
+            cudaError_t e = enqueue_steps(b, nsteps, &nk);
+            g_launches.store(before);  // captured launches run at replay
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "cme_step: capture");
+            CME_CUDA(e2, "cme_step: end capture");
+            cudaGraphExec_t exec;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CME_CUDA(e, "cme_step: graph instantiate");
+            it = b->graphs.emplace(key, std::make_pair(exec, nk)).first;
+        }
+        g_launches += it->second.second;
+        CME_CUDA(cudaGraphLaunch(it->second.first, b->stream), "cme_step: graph launch");
+    } else {
+        CME_CUDA(enqueue_steps(b, nsteps, nullptr), "cme_step: kernel launch");
+    }
+    b->tau += h * (double)nsteps;
+    return CME_OK;
+}
+
+int cme_synchronize(cme_batch b)
+{
+    if (!b)
+        return fail(CME_ERR_INVALID_ARG, "cme_synchronize: NULL batch");
+    CME_CUDA(cudaStreamSynchronize(b->stream), "cme_synchronize");
+    std::vector<int> st(b->count);
+    CME_CUDA(cudaMemcpy(st.data(), b->status_d, b->count * 4, cudaMemcpyDeviceToHost),
+             "cme_synchronize: status");
+    for (int i = 0; i < b->count; ++i)
+        if (st[i])
+            return fail(CME_ERR_NONFINITE, "instance %d has a non-finite field value", i);
+    return CME_OK;
+}
+
+int cme_status(cme_batch b, int* per_instance)
+{
+    if (!b || !per_instance)
+        return fail(CME_ERR_INVALID_ARG, "cme_status: NULL argument");
+    CME_CUDA(cudaStreamSynchronize(b->stream), "cme_status");
+    CME_CUDA(cudaMemcpy(per_instance, b->status_d, b->count * 4, cudaMemcpyDeviceToHost),
+             "cme_status: copy");
+    return CME_OK;
+}
+
+int cme_get_time(cme_batch b, double* tau)
+{
+    if (!b || !tau)
+        return fail(CME_ERR_INVALID_ARG, "cme_get_time: NULL argument");
+    *tau = b->tau;
+    return CME_OK;
+}
+
+int cme_set_time(cme_batch b, double tau)
+{
+    if (!b || !std::isfinite(tau))
+        return fail(CME_ERR_INVALID_ARG, "cme_set_time: invalid argument");
+    b->tau = tau;
+    return CME_OK;
+}
+
+int cme_get_state(cme_batch b, double* buf, int where)
+{
+    if (!b || !buf || (where != CME_HOST && where != CME_DEVICE))
+        return fail(CME_ERR_INVALID_ARG, "cme_get_state: invalid argument");
+    double2* dst = where == CME_DEVICE ? (double2*)buf : b->stage;
+    ++g_launches;
+    CME_CUDA(launch_export(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, b->hi,
+                           b->lo, dst, 1, b->omega, b->sigma_d, b->tau, b->stream),
+             "cme_get_state: export");
+    if (where == CME_HOST) {
+        CME_CUDA(cudaMemcpyAsync(buf, b->stage, b->total * 16, cudaMemcpyDeviceToHost, b->stream),
+                 "cme_get_state: copy");
+        CME_CUDA(cudaStreamSynchronize(b->stream), "cme_get_state: sync");
+    }
+    return CME_OK;
+}
+
+int cme_set_state(cme_batch b, const double* buf, int where)
+{
+    if (!b || !buf || (where != CME_HOST && where != CME_DEVICE))
+        return fail(CME_ERR_INVALID_ARG, "cme_set_state: invalid argument");
+    const double2* src = (const double2*)buf;
+    if (where == CME_HOST) {
+        CME_CUDA(cudaMemcpyAsync(b->stage, buf, b->total * 16, cudaMemcpyHostToDevice, b->stream),
+                 "cme_set_state: copy");
+        src = b->stage;
+    }
+    ++g_launches;
+    CME_CUDA(launch_import(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, src, b->hi,
+                           b->lo, b->stream),
+             "cme_set_state: import");
+    CME_CUDA(cudaMemsetAsync(b->status_d, 0, b->count * 4, b->stream), "cme_set_state: status");
+    if (where == CME_HOST)
+        CME_CUDA(cudaStreamSynchronize(b->stream), "cme_set_state: sync");
+    return CME_OK;
+}
+
+int cme_spectrum(cme_batch b, int idx, int what, double* out)
+{
+    if (!b || !out || idx < -1 || idx >= b->count ||
+        (what != CME_POWER && what != CME_FIELD_D && what != CME_FIELD_EQ1))
+        return fail(CME_ERR_INVALID_ARG, "cme_spectrum: invalid argument");
+    ++g_launches;
+    CME_CUDA(launch_export(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, b->hi,
+                           b->lo, b->stage, what, b->omega, b->sigma_d, b->tau, b->stream),
+             "cme_spectrum: export");
+    const size_t per = what == CME_POWER ? 8 : 16;
+    const long long first = idx < 0 ? 0 : b->off_h[idx];
+    const long long n = idx < 0 ? b->total : b->N_h[idx];
+    CME_CUDA(cudaMemcpyAsync(out, (char*)b->stage + first * per, n * per, cudaMemcpyDeviceToHost,
+                             b->stream),
+             "cme_spectrum: copy");
+    CME_CUDA(cudaStreamSynchronize(b->stream), "cme_spectrum: sync");
+    return CME_OK;
+}
+
+int cme_checkpoint_size(cme_batch b, size_t* bytes)
+{
+    if (!b || !bytes)
+        return fail(CME_ERR_INVALID_ARG, "cme_checkpoint_size: NULL argument");
+    *bytes = sizeof(double) + (size_t)b->total * b->elem * (b->prec == PREC_FP32 ? 2 : 1);
+    return CME_OK;
+}
+
+int cme_checkpoint_save(cme_batch b, void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (!b || !host_buf || cme_checkpoint_size(b, &need) || bytes < need)
+        return fail(CME_ERR_INVALID_ARG, "cme_checkpoint_save: buffer too small or NULL");
+    char* p = (char*)host_buf;
+    std::memcpy(p, &b->tau, sizeof(double));
+    const size_t fb = (size_t)b->total * b->elem;
+    CME_CUDA(cudaMemcpyAsync(p + sizeof(double), b->hi, fb, cudaMemcpyDeviceToHost, b->stream),
+             "cme_checkpoint_save: copy");
+    if (b->prec == PREC_FP32)
+        CME_CUDA(cudaMemcpyAsync(p + sizeof(double) + fb, b->lo, fb, cudaMemcpyDeviceToHost, b->stream),
+                 "cme_checkpoint_save: copy");
+    CME_CUDA(cudaStreamSynchronize(b->stream), "cme_checkpoint_save: sync");
+    return CME_OK;
+}
+
+int cme_checkpoint_load(cme_batch b, const void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (!b || !host_buf || cme_checkpoint_size(b, &need) || bytes < need)
+        return fail(CME_ERR_INVALID_ARG, "cme_checkpoint_load: buffer too small or NULL");
+    const char* p = (const char*)host_buf;
+    double tau;
+    std::memcpy(&tau, p, sizeof(double));
+    const size_t fb = (size_t)b->total * b->elem;
+    CME_CUDA(cudaMemcpyAsync(b->hi, p + sizeof(double), fb, cudaMemcpyHostToDevice, b->stream),
+             "cme_checkpoint_load: copy");
+    if (b->prec == PREC_FP32)
+        CME_CUDA(cudaMemcpyAsync(b->lo, p + sizeof(double) + fb, fb, cudaMemcpyHostToDevice, b->stream),
+                 "cme_checkpoint_load: copy");
+    CME_CUDA(cudaMemsetAsync(b->status_d, 0, b->count * 4, b->stream), "cme_checkpoint_load: status");
+    CME_CUDA(cudaStreamSynchronize(b->stream), "cme_checkpoint_load: sync");
+    b->tau = tau;
+    return CME_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int run_diag(cme_batch b, int mode, double* out, int where, int reorder_centred, const char* who)
+{
+    if (!b || !out || (where != CME_HOST && where != CME_DEVICE))
+        return fail(CME_ERR_INVALID_ARG, "%s: invalid argument", who);
+    for (auto& g : b->groups) {
+        StepArgs a = group_args(b, g);
+        a.diag_mode = mode;
+        a.diag_out = b->diag;
+        ++g_launches;
+        cudaError_t e = b->prec == PREC_FP64 ? launch_diag_fp64(g.logN, g.R, a, b->stream)
+                                             : launch_diag_fp32(g.logN, g.R, a, b->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, who);
+    }
+    double2* dst = where == CME_DEVICE ? (double2*)out : b->stage;
+    ++g_launches;
+    CME_CUDA(launch_export_plain(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off,
+                                 b->diag, dst, reorder_centred, b->stream),
+             who);
+    if (where == CME_HOST) {
+        CME_CUDA(cudaMemcpyAsync(out, b->stage, b->total * 16, cudaMemcpyDeviceToHost, b->stream), who);
+        CME_CUDA(cudaStreamSynchronize(b->stream), who);
+    }
+    return CME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cme_transform(cme_batch b, int sign, double* out, int where)
+{
+    if (sign != 1 && sign != -1)
+        return fail(CME_ERR_INVALID_ARG, "cme_transform: sign must be +1 or -1");
+    return run_diag(b, sign > 0 ? DIAG_IDFT : DIAG_DFT, out, where, 0, "cme_transform");
+}
+
+int cme_eval_rhs(cme_batch b, double* out, int where)
+{
+    return run_diag(b, DIAG_RHS, out, where, 1, "cme_eval_rhs");
+}
+
+int cme_fma_peak(int precision, double* flops_per_s)
+{
+    if (!flops_per_s || (precision != CME_FP32 && precision != CME_FP64))
+        return fail(CME_ERR_INVALID_ARG, "cme_fma_peak: invalid argument");
+    g_launches += 4;
+    CME_CUDA(run_fma_peak(precision == CME_FP32 ? PREC_FP32 : PREC_FP64, flops_per_s), "cme_fma_peak");
+    return CME_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,353 @@
+// Device core of the CME integrator: register/shared-memory Stockham transforms over the mode
+// number (Eq. 4), the Kerr term, the pump, and the RK4IP and Strang step bodies (Sec. 2).
+//
+// Thread mapping.  One instance of N modes is handled by P = N/R threads; thread t holds the
+// R field values at transform positions t + j*P (j = 0..R-1) in registers for the whole launch.
+// A transform is a sequence of radix-R Stockham passes (the last one may use a smaller radix);
+// between passes the group exchanges values through a padded shared-memory buffer.  Both the
+// inverse transform (sign +1) and the forward transform (sign -1) start and end with the same
+// register assignment, so the Kerr term, the pump and every Runge-Kutta combination are
+// register-local.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "cme_internal.h"
+
+#define CME_DEV __device__ __forceinline__
+#define CME_HD __host__ __device__
+
+namespace cme {
+
+template <typename T>
+struct cx {
+    T re, im;
+};
+
+template <typename T>
+CME_DEV cx<T> cadd(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+CME_DEV cx<T> csub(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+CME_DEV cx<T> cmul(cx<T> a, cx<T> b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+// a * conj(b)
+template <typename T>
+CME_DEV cx<T> cmulc(cx<T> a, cx<T> b) { return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im}; }
+template <typename T>
+CME_DEV cx<T> cscale(cx<T> a, T s) { return {a.re * s, a.im * s}; }
+// a + s * b
+template <typename T>
+CME_DEV cx<T> caxpy(cx<T> a, T s, cx<T> b) { return {a.re + s * b.re, a.im + s * b.im}; }
+
+template <typename T> struct v2;
+template <> struct v2<float> { using type = float2; };
+template <> struct v2<double> { using type = double2; };
+
+template <typename T>
+CME_DEV cx<T> gload(const void* p, long long i)
+{
+    const typename v2<T>::type v = __ldg(reinterpret_cast<const typename v2<T>::type*>(p) + i);
+    return {v.x, v.y};
+}
+template <typename T>
+CME_DEV cx<T> load(const void* p, long long i)
+{
+    const typename v2<T>::type v = reinterpret_cast<const typename v2<T>::type*>(p)[i];
+    return {v.x, v.y};
+}
+template <typename T>
+CME_DEV void store(void* p, long long i, cx<T> a)
+{
+    typename v2<T>::type v;
+    v.x = a.re;
+    v.y = a.im;
+    reinterpret_cast<typename v2<T>::type*>(p)[i] = v;
+}
+
+// ----------------------------------------------------------------------------------------
+// Transform plan: N = 2^LOGN, R values per thread, NS passes, last radix 2^LOG_LAST.
+// ----------------------------------------------------------------------------------------
+CME_HD constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+template <int LOGN, int R>
+struct Plan {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int LOGR = ilog2(R);
+    static_assert((1 << LOGR) == R && R >= 2 && R <= 16, "radix");
+    static_assert(N >= R, "N >= R");
+    static constexpr int P = N / R;
+    static constexpr int NS = (LOGN + LOGR - 1) / LOGR;
+    static constexpr int LOG_LAST = LOGN - (NS - 1) * LOGR;
+    CME_HD static constexpr int radix(int s) { return s < NS - 1 ? R : (1 << LOG_LAST); }
+    CME_HD static constexpr int L(int s) { return 1 << (s * LOGR); }
+    static constexpr int NTW = (NS - 1) * (R - 1);  // register twiddles, stages 1..NS-1
+    CME_HD static constexpr int pad(int p) { return p + (p >> 4); }
+    static constexpr int BUF = N + N / 16 + 1;      // padded buffer length (elements)
+};
+
+// exp(2 pi i k / 16), k = 0..15 (compile-time constants of the in-register DFTs)
+CME_DEV constexpr double c16(int k)
+{
+    constexpr double t[16] = {1.0,
+                              0.92387953251128675613,
+                              0.70710678118654752440,
+                              0.38268343236508977173,
+                              0.0,
+                              -0.38268343236508977173,
+                              -0.70710678118654752440,
+                              -0.92387953251128675613,
+                              -1.0,
+                              -0.92387953251128675613,
+                              -0.70710678118654752440,
+                              -0.38268343236508977173,
+                              0.0,
+                              0.38268343236508977173,
+                              0.70710678118654752440,
+                              0.92387953251128675613};
+    return t[k & 15];
+}
+CME_DEV constexpr double s16(int k) { return c16(k - 4); }
+
+// z * exp(S * 2 pi i k / 16) with the trivial angles done without multiplies.
+template <int S, int K, typename T>
+CME_DEV cx<T> rot16(cx<T> z)
+{
+    constexpr int k = ((S > 0 ? K : 16 - K) % 16 + 16) % 16;
+    if constexpr (k == 0) {
+        return z;
+    } else if constexpr (k == 4) {
+        return {-z.im, z.re};
+    } else if constexpr (k == 8) {
+        return {-z.re, -z.im};
+    } else if constexpr (k == 12) {
+        return {z.im, -z.re};
+    } else if constexpr (k == 2 || k == 6 || k == 10 || k == 14) {
+        // (+-1 +- i)/sqrt(2)
+        constexpr T h = (T)0.70710678118654752440;
+        constexpr T cr = (k == 2 || k == 14) ? h : -h;
+        constexpr T ci = (k == 2 || k == 6) ? h : -h;
+        return {(z.re * (cr > 0 ? 1 : -1) - z.im * (ci > 0 ? 1 : -1)) * h,
+                (z.re * (ci > 0 ? 1 : -1) + z.im * (cr > 0 ? 1 : -1)) * h};
+    } else {
+        constexpr T c = (T)c16(k);
+        constexpr T s = (T)s16(k);
+        return {z.re * c - z.im * s, z.re * s + z.im * c};
+    }
+}
+
+CME_HD constexpr int bitrev(int x, int bits)
+{
+    int r = 0;
+    for (int i = 0; i < bits; ++i)
+        if (x & (1 << i))
+            r |= 1 << (bits - 1 - i);
+    return r;
+}
+
+// In-register DFT of size r (natural order in and out): v[k] = sum_j v[j] exp(S 2 pi i jk/r).
+// Radix-2 decimation in frequency; the bit reversal at the end is a register renaming.
+template <int r, int S, int span, typename T>
+CME_DEV void dft_stage(cx<T> (&v)[r])
+{
+    if constexpr (span >= 1) {
+#pragma unroll
+        for (int blk = 0; blk < r; blk += 2 * span) {
+#pragma unroll
+            for (int j = 0; j < span; ++j) {
+                const cx<T> a = v[blk + j], b = v[blk + j + span];
+                v[blk + j] = cadd(a, b);
+                v[blk + j + span] = csub(a, b);
+            }
+        }
+        // twiddles exp(S 2 pi i j / (2 span)) on the lower halves
+#pragma unroll
+        for (int blk = 0; blk < r; blk += 2 * span) {
+            if constexpr (span >= 2) {
+                v[blk + span + 1] = rot16<S, 16 / (2 * span) * 1>(v[blk + span + 1]);
+            }
+            if constexpr (span >= 4) {
+                v[blk + span + 2] = rot16<S, 16 / (2 * span) * 2>(v[blk + span + 2]);
+                v[blk + span + 3] = rot16<S, 16 / (2 * span) * 3>(v[blk + span + 3]);
+            }
+            if constexpr (span >= 8) {
+                v[blk + span + 4] = rot16<S, 4>(v[blk + span + 4]);
+                v[blk + span + 5] = rot16<S, 5>(v[blk + span + 5]);
+                v[blk + span + 6] = rot16<S, 6>(v[blk + span + 6]);
+                v[blk + span + 7] = rot16<S, 7>(v[blk + span + 7]);
+            }
+        }
+        dft_stage<r, S, span / 2>(v);
+    }
+}
+
+template <int r, int S, typename T>
+CME_DEV void dft(cx<T> (&v)[r])
+{
+    static_assert(r <= 16, "in-register DFT up to 16");
+    if constexpr (r > 1) {
+        dft_stage<r, S, r / 2>(v);
+        cx<T> t[r];
+#pragma unroll
+        for (int k = 0; k < r; ++k)
+            t[k] = v[bitrev(k, ilog2(r))];
+#pragma unroll
+        for (int k = 0; k < r; ++k)
+            v[k] = t[k];
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// Shared-memory exchange buffer: float2 words for FP32, separate re/im arrays for FP64 (so
+// both are 8-byte accesses with the same bank pattern).
+// ----------------------------------------------------------------------------------------
+template <typename T> struct Xbuf;
+template <>
+struct Xbuf<float> {
+    float2* p;
+    CME_DEV void put(int i, cx<float> v) const { p[i] = make_float2(v.re, v.im); }
+    CME_DEV cx<float> get(int i) const
+    {
+        const float2 a = p[i];
+        return {a.x, a.y};
+    }
+    static constexpr int words_per_elem = 1;  // in 8-byte words
+};
+template <>
+struct Xbuf<double> {
+    double* re;
+    double* im;
+    CME_DEV void put(int i, cx<double> v) const
+    {
+        re[i] = v.re;
+        im[i] = v.im;
+    }
+    CME_DEV cx<double> get(int i) const { return {re[i], im[i]}; }
+    static constexpr int words_per_elem = 2;
+};
+
+template <bool WARP>
+CME_DEV void group_sync()
+{
+    if constexpr (WARP)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
+// ----------------------------------------------------------------------------------------
+// Transform of one group: x holds positions t + j*P; sign S (+1 inverse / time samples,
+// -1 forward).  tw holds exp(+2 pi i j k/(L r)) for the passes s >= 1.
+// ----------------------------------------------------------------------------------------
+template <typename T, int LOGN, int R, bool WARP>
+struct Transform {
+    using PL = Plan<LOGN, R>;
+    static constexpr int N = PL::N, P = PL::P, NS = PL::NS;
+
+    template <int s, int S>
+    CME_DEV static void pass(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1])
+    {
+        constexpr int r = PL::radix(s), Q = R / r;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            cx<T> v[r];
+#pragma unroll
+            for (int j = 0; j < r; ++j)
+                v[j] = x[q + j * Q];
+            if constexpr (s > 0) {
+#pragma unroll
+                for (int j = 1; j < r; ++j) {
+                    const cx<T> w = tw[(s - 1) * (R - 1) + q * (r - 1) + (j - 1)];
+                    v[j] = (S > 0) ? cmul(v[j], w) : cmulc(v[j], w);
+                }
+            }
+            dft<r, S>(v);
+#pragma unroll
+            for (int j = 0; j < r; ++j)
+                x[q + j * Q] = v[j];
+        }
+    }
+
+    template <int s>
+    CME_DEV static void exchange(cx<T> (&x)[R], const Xbuf<T>& b, int t)
+    {
+        constexpr int r = PL::radix(s), Q = R / r, L = PL::L(s);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int tp = t + q * P;
+            const int k = tp & (L - 1);
+            const int base = (tp - k) * r + k;
+#pragma unroll
+            for (int j = 0; j < r; ++j)
+                b.put(PL::pad(base + j * L), x[q + j * Q]);
+        }
+        group_sync<WARP>();
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            x[j] = b.get(PL::pad(t + j * P));
+    }
+
+    template <int s, int S>
+    CME_DEV static void run_from(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1],
+                                 const Xbuf<T> (&buf)[2], int& par, int t)
+    {
+        pass<s, S>(x, tw);
+        if constexpr (s + 1 < NS) {
+            exchange<s>(x, buf[par], t);
+            par ^= 1;
+            run_from<s + 1, S>(x, tw, buf, par, t);
+        }
+    }
+
+    template <int S>
+    CME_DEV static void run(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1],
+                            const Xbuf<T> (&buf)[2], int& par, int t)
+    {
+        run_from<0, S>(x, tw, buf, par, t);
+    }
+
+    // Twiddles exp(2 pi i j k / (L r)), k = (t + qP) mod L, from the table exp(2 pi i m/N).
+    template <int s>
+    CME_DEV static void load_tw_from(cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1], const void* table, int t)
+    {
+        if constexpr (s < NS) {
+            constexpr int r = PL::radix(s), Q = R / r, L = PL::L(s);
+            constexpr int stride = N / (L * r);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int k = (t + q * P) & (L - 1);
+#pragma unroll
+                for (int j = 1; j < r; ++j)
+                    tw[(s - 1) * (R - 1) + q * (r - 1) + (j - 1)] =
+                        gload<T>(table, (j * k * stride) & (N - 1));
+            }
+            load_tw_from<s + 1>(tw, table, t);
+        }
+    }
+    CME_DEV static void load_tw(cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1], const void* table, int t)
+    {
+        if constexpr (NS > 1)
+            load_tw_from<1>(tw, table, t);
+    }
+};
+
+// Compensated update (hi, lo) += d with an exact two-sum of hi and (lo + d).
+template <typename T, bool COMP>
+CME_DEV void accumulate(cx<T>& hi, cx<T>& lo, cx<T> d)
+{
+    if constexpr (COMP) {
+        const T yr = lo.re + d.re, yi = lo.im + d.im;
+        const T sr = hi.re + yr, si = hi.im + yi;
+        const T br = sr - hi.re, bi = si - hi.im;
+        lo.re = (hi.re - (sr - br)) + (yr - br);
+        lo.im = (hi.im - (si - bi)) + (yi - bi);
+        hi.re = sr;
+        hi.im = si;
+    } else {
+        hi.re += d.re;
+        hi.im += d.im;
+    }
+}
+
+}  // namespace cme

@@ -1,0 +1,70 @@
+// Launch helpers shared by the per-precision kernel translation units.
+#pragma once
+
+#include "cme_step.cuh"
+
+namespace cme {
+
+// Every compiled (log2 N, values per thread) pair.  Values per thread R: 8 is the default;
+// 4 and 16 are alternative launch shapes where they fit in registers without spilling.
+#define CME_FOR_EACH_SHAPE(X)          \
+    X(2, 4)                            \
+    X(3, 8)                            \
+    X(4, 8) X(4, 16)                   \
+    X(5, 8) X(5, 16)                   \
+    X(6, 8) X(6, 4) X(6, 16)           \
+    X(7, 8) X(7, 4) X(7, 16)           \
+    X(8, 8) X(8, 4) X(8, 16)           \
+    X(9, 8) X(9, 4)                    \
+    X(10, 8) X(10, 4)                  \
+    X(11, 8)                           \
+    X(12, 8)
+
+template <typename T>
+inline size_t smem_bytes_for(int logN, int G)
+{
+    const int N = 1 << logN;
+    const int BUF = N + N / 16 + 1;
+    const int W = sizeof(T) == 4 ? 1 : 2;
+    return (size_t)G * 2 * W * BUF * 8;
+}
+
+template <typename KernelT>
+inline cudaError_t prepare_smem(KernelT k, size_t smem)
+{
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+template <typename T, int LOGN, int R, int METHOD>
+inline cudaError_t launch_step_shape(const StepArgs& a, cudaStream_t s)
+{
+    constexpr int P = Plan<LOGN, R>::P;
+    const int threads = P * a.G;
+    const int blocks = (a.ninst + a.G - 1) / a.G;
+    const size_t smem = smem_bytes_for<T>(LOGN, a.G);
+    auto k = step_kernel<T, LOGN, R, METHOD>;
+    cudaError_t e = prepare_smem(k, smem);
+    if (e != cudaSuccess)
+        return e;
+    k<<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN, int R>
+inline cudaError_t launch_diag_shape(const StepArgs& a, cudaStream_t s)
+{
+    constexpr int P = Plan<LOGN, R>::P;
+    const int threads = P * a.G;
+    const int blocks = (a.ninst + a.G - 1) / a.G;
+    const size_t smem = smem_bytes_for<T>(LOGN, a.G);
+    auto k = diag_kernel<T, LOGN, R>;
+    cudaError_t e = prepare_smem(k, smem);
+    if (e != cudaSuccess)
+        return e;
+    k<<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace cme

@@ -116,16 +116,18 @@ def plain64(nsteps: int = 2000) -> Workload:
 
 
 def sweep512(n_inst: int = 256, nsteps: int = 20000, N: int = 512,
-             indices: Optional[Sequence[int]] = None) -> Workload:
+             indices: Optional[Sequence[int]] = None, seed_offset: int = 0) -> Workload:
     """N=512 x 256 instances, sigma swept linearly -2..10, A_in=2.5, D2=0.02, noise 1e-6,
     h=5e-4, 20000 steps.  `indices` selects a subset of the full 256-instance sweep (the
-    selected instances keep their sweep parameters and seeds)."""
+    selected instances keep their sweep parameters and seeds).  `seed_offset` shifts the noise
+    seeds (another replica of the sweep with independent noise)."""
     full = 256
     idx = list(range(n_inst)) if indices is None else list(indices)
     insts = []
     for b in idx:
         sigma = -2.0 + 12.0 * b / (full - 1)
-        insts.append(make_instance(N, 0.02, 0.0, sigma, 2.5, 1e-6, seed=1307 + 1000 * 2 + b))
+        insts.append(make_instance(N, 0.02, 0.0, sigma, 2.5, 1e-6,
+                                   seed=1307 + 1000 * 2 + b + seed_offset))
     return Workload("sweep_n512_b256" if indices is None and n_inst == 256 else "sweep_n512_subset",
                     insts, 5e-4, nsteps,
                     "N=512, sigma in [-2,10], A_in=2.5, D2=0.02, h=5e-4")

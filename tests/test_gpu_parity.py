@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 batches agree with the oracle to 1e-10 relative L2 of the final field; FP32
+batches to 1e-4 (the stated bound for the FP32-field / FP64-propagator path).  Hot-path pieces
+(transforms, the right-hand side) are compared element by element at tighter bounds."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from oracle import fft_engine
+from paper_1307_3428_gb300 import cme
+from paper_1307_3428_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {cme.FP64: 1e-10, cme.FP32: 1e-4}
+SIZES = [4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    cme.load()
+
+
+def rel(x, y):
+    return float(np.linalg.norm(np.asarray(x) - np.asarray(y)) / np.linalg.norm(np.asarray(y)))
+
+
+def batch_of(insts, prec, integ=cme.RK4IP, **kw):
+    return cme.Batch([cme.Instance.from_workload(i) for i in insts], precision=prec,
+                     integrator=integ, **kw)
+
+
+# ---------------------------------------------------------------------------- hot-path pieces
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N", SIZES)
+def test_transform_matches_naive_dft(N, prec):
+    insts = [wl.random_instance(N, 500 + k) for k in range(3)]
+    b = batch_of(insts, prec)
+    for sign in (+1, -1):
+        got = b.split(b.transform(sign))
+        for g, inst in zip(got, insts):
+            if sign > 0:
+                ref = oracle.dft(inst.D0, +1)
+            else:  # sum_mu D_mu e^{-2 pi i j mu/N}: the +1 transform of the mirrored field
+                ref = np.conj(oracle.dft(np.conj(inst.D0), +1))
+            tol = 1e-13 if prec == cme.FP64 else 2e-6
+            assert np.max(np.abs(g - ref)) <= tol * np.max(np.abs(ref)) * max(1, np.log2(N)), (sign,)
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 64, 128, 256])
+def test_rhs_matches_direct_sum(N, prec):
+    insts = [wl.random_instance(N, 700 + k, A_in=1.1 - 0.3j * k, g0=0.5 + 0.25 * k)
+             for k in range(3)]
+    b = batch_of(insts, prec)
+    got = b.split(b.eval_rhs())
+    for g, inst in zip(got, insts):
+        ref = oracle.rhs(inst.D0, inst.g0, inst.kappa_ext, inst.A_in)
+        tol = 1e-12 if prec == cme.FP64 else 3e-6
+        assert np.max(np.abs(g - ref)) <= tol * np.max(np.abs(ref)) * max(1, np.log2(N))
+
+
+def test_rhs_n512_direct_sum_fp64():
+    inst = wl.sweep512(indices=[37]).instances[0]
+    b = batch_of([inst], cme.FP64)
+    got = b.eval_rhs()
+    ref = oracle.rhs(inst.D0, inst.g0, inst.kappa_ext, inst.A_in)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------- integrators
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_plain_n64_full_horizon(prec):
+    """N=64, one instance, h=1e-3, 2000 RK4IP steps against the direct-sum oracle."""
+    w = wl.plain64()
+    inst = w.instances[0]
+    b = batch_of([inst], prec)
+    b.step(w.h, w.nsteps)
+    b.synchronize()
+    got = b.get_state()
+    ref = oracle.integrate(inst, w.h, w.nsteps, oracle.RK4IP)
+    err = rel(got, ref)
+    assert err <= TOL[prec], err
+    # the power spectrum too
+    assert rel(b.spectrum(cme.POWER), np.abs(ref) ** 2) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N", SIZES)
+def test_rk4ip_every_size_short(N, prec):
+    """Random fields on all modes (every mode of the comb active), 20 steps, ragged batch."""
+    amp = 0.3 * min(1.0, np.sqrt(64.0 / N))       # keeps |a_j|^2 = O(1) at every N
+    insts = [wl.random_instance(N, 900 + k, amp=amp, sigma=0.5 * k, A_in=1.0 + 0.2j * k)
+             for k in range(5)]
+    b = batch_of(insts, prec)
+    b.step(1e-3, 20)
+    got = b.split(b.get_state())
+    if N <= 64:
+        refs = [oracle.integrate(i, 1e-3, 20, oracle.RK4IP) for i in insts]
+    else:
+        refs = fft_engine.rk4ip(fft_engine.Batch(insts), 1e-3, 20)
+    for g, r in zip(got, refs):
+        assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N", [4, 16, 64, 512])
+def test_strang_matches_oracle(N, prec):
+    amp = 0.3 * min(1.0, np.sqrt(64.0 / N))
+    insts = [wl.random_instance(N, 1100 + k, amp=amp, sigma=1.0 + k, A_in=1.2) for k in range(3)]
+    b = batch_of(insts, prec, cme.STRANG)
+    b.step(2e-3, 200)
+    got = b.split(b.get_state())
+    if N <= 16:
+        refs = [oracle.integrate(i, 2e-3, 200, oracle.STRANG) for i in insts]
+    else:
+        refs = fft_engine.strang(fft_engine.Batch(insts), 2e-3, 200)
+    for g, r in zip(got, refs):
+        assert rel(g, r) <= (1e-11 if prec == cme.FP64 else 1e-5)
+
+
+def test_strang_n64_direct_definition():
+    w = wl.plain64(nsteps=300)
+    inst = w.instances[0]
+    for prec in (cme.FP64, cme.FP32):
+        b = batch_of([inst], prec, cme.STRANG)
+        b.step(w.h, w.nsteps)
+        ref = oracle.integrate(inst, w.h, w.nsteps, oracle.STRANG)
+        assert rel(b.get_state(), ref) <= TOL[prec]
+
+
+def sweep_indices():
+    # both ends, the MI-unstable band around sigma ~ 2.7-2.9, and a few in between
+    return [0, 1, 57, 100, 102, 105, 128, 200, 254, 255]
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_sweep512_full_batch_full_horizon(prec):
+    """N=512 x 256 instances, 20000 RK4IP steps in the launch configuration of the benchmark
+    (one graph replay); sampled instances against the FP64 oracle (Eq. 4 engine), every
+    instance finite and status clean."""
+    w = wl.sweep512()
+    b = batch_of(w.instances, prec, use_graph=True)
+    b.step(w.h, w.nsteps)
+    b.synchronize()
+    assert not b.status().any()
+    got = b.split(b.get_state())
+    idx = sweep_indices()
+    sub = [w.instances[i] for i in idx]
+    refs = fft_engine.rk4ip(fft_engine.Batch(sub), w.h, w.nsteps)
+    errs = [rel(got[i], r) for i, r in zip(idx, refs)]
+    assert max(errs) <= TOL[prec], errs
+    for g in got:
+        assert np.all(np.isfinite(g))
+
+
+def test_sweep512_short_direct_sum():
+    """Two instances of the sweep, 3 steps, against the direct O(N^3) definition."""
+    w = wl.sweep512(indices=[3, 150])
+    for prec in (cme.FP64, cme.FP32):
+        b = batch_of(w.instances, prec)
+        b.step(w.h, 3)
+        got = b.split(b.get_state())
+        for g, inst in zip(got, w.instances):
+            ref = oracle.integrate(inst, w.h, 3, oracle.RK4IP)
+            assert rel(g, ref) <= (1e-13 if prec == cme.FP64 else 1e-6)
+
+
+# ---------------------------------------------------------------------------- launch paths
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_graph_chunking_and_packing_are_bitwise_identical(prec):
+    insts = wl.sweep512(indices=range(0, 256, 23)).instances
+    ref = batch_of(insts, prec)
+    ref.step(5e-4, 60)
+    base = ref.get_state()
+    for kw in (dict(use_graph=True), dict(steps_per_launch=7), dict(inst_per_cta=2),
+               dict(use_graph=True, steps_per_launch=25)):
+        b = batch_of(insts, prec, **kw)
+        b.step(5e-4, 60)
+        assert np.array_equal(b.get_state(), base), kw
+
+
+@pytest.mark.parametrize("radix", [4, 8])
+def test_radix_variants_agree(radix):
+    insts = wl.sweep512(indices=[10, 90, 180]).instances
+    b = batch_of(insts, cme.FP64, radix=radix)
+    b.step(5e-4, 50)
+    refs = fft_engine.rk4ip(fft_engine.Batch(insts), 5e-4, 50)
+    for g, r in zip(b.split(b.get_state()), refs):
+        assert rel(g, r) <= 1e-12
+
+
+def test_uneven_sizes_in_one_batch():
+    insts = [wl.random_instance(N, 1300 + N, amp=0.2 * min(1.0, np.sqrt(64.0 / N)))
+             for N in (4, 16, 16, 64, 256, 256, 1024)]
+    for prec in (cme.FP64, cme.FP32):
+        b = batch_of(insts, prec)
+        b.step(1e-3, 10)
+        for g, inst in zip(b.split(b.get_state()), insts):
+            r = fft_engine.rk4ip(fft_engine.Batch([inst]), 1e-3, 10)[0]
+            assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
+
+
+def test_zero_steps_is_a_noop_and_bad_h_is_rejected():
+    inst = wl.random_instance(32, 5)
+    b = batch_of([inst], cme.FP64)
+    s0 = b.get_state()
+    b.step(1e-3, 0)
+    assert np.array_equal(b.get_state(), s0)
+    for h in (0.0, -1e-3, float("nan"), float("inf")):
+        with pytest.raises(cme.CmeError) as e:
+            b.step(h, 1)
+        assert e.value.code == -1
+    with pytest.raises(cme.CmeError):
+        b.step(1e-3, -1)
+
+
+def test_nonfinite_field_sets_status():
+    good = wl.random_instance(16, 1)
+    bad = wl.random_instance(16, 2, amp=1e200)   # overflows to inf within a few steps
+    b = batch_of([good, bad, good], cme.FP64)
+    b.step(1e-2, 5)
+    st = b.status()
+    assert st[0] == 0 and st[1] == 1 and st[2] == 0
+    with pytest.raises(cme.CmeError) as e:
+        b.synchronize()
+    assert e.value.code == -4
+    b.set_state(np.concatenate([good.D0, good.D0, good.D0]))
+    assert not b.status().any()
+
+
+def test_state_roundtrip_checkpoint_and_resume_bitwise():
+    insts = wl.sweep512(indices=[5, 77]).instances
+    for prec in (cme.FP64, cme.FP32):
+        a = batch_of(insts, prec)
+        a.step(5e-4, 40)
+        blob = a.checkpoint()
+        a.step(5e-4, 40)
+        fin = a.get_state()
+        b = batch_of(insts, prec)
+        b.restore(blob)
+        assert abs(b.time() - 40 * 5e-4) < 1e-15
+        b.step(5e-4, 40)
+        assert np.array_equal(b.get_state(), fin)
+        # FP64 state export/import round trip
+        s = a.get_state()
+        a.set_state(s)
+        assert np.array_equal(a.get_state(), s)
+
+
+def test_eq1_frame_output():
+    w = wl.plain64(nsteps=200)
+    inst = w.instances[0]
+    b = batch_of([inst], cme.FP64)
+    b.step(w.h, w.nsteps)
+    D = b.get_state()
+    A = b.spectrum(cme.FIELD_EQ1)
+    assert rel(A, oracle.to_lab_frame(inst, D, w.h * w.nsteps)) <= 1e-14
+    assert rel(b.spectrum(cme.FIELD_D), D) == 0.0
+
+
+def test_torch_allocator_and_stream():
+    import torch
+    cme.use_torch_allocator()
+    try:
+        s = torch.cuda.Stream()
+        inst = wl.plain64(nsteps=100).instances[0]
+        b = cme.Batch([cme.Instance.from_workload(inst)], precision=cme.FP64,
+                      stream=s.cuda_stream)
+        b.step(1e-3, 100)
+        ref = oracle.integrate(inst, 1e-3, 100, oracle.RK4IP)
+        assert rel(b.get_state(), ref) <= 1e-11
+        b.close()
+    finally:
+        cme.load().cme_set_allocator(cme.ALLOC_FN(), cme.FREE_FN(), None)
