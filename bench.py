@@ -220,7 +220,8 @@ def run_gpu(args, world, rank, local):
     mode_steps = count * N * nsteps
 
     insts = [cme.Instance.from_workload(i) for i in w.instances]
-    b32 = cme.Batch(insts, precision=cme.FP32, use_graph=True)
+    b32 = cme.Batch(insts, precision=cme.FP32, use_graph=True, radix=args.radix,
+                    inst_per_cta=args.inst_per_cta)
     stream = torch.cuda.ExternalStream(b32.stream)
     D0 = np.concatenate([i.D0 for i in w.instances])
     d0_dev = torch.from_numpy(D0.view(np.float64).copy()).cuda()
@@ -280,7 +281,7 @@ def run_gpu(args, world, rank, local):
             traffic = ent.get("dram_bytes_per_launch")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "step_kernel<float, 9, 8, RK4IP>",
+                "kernel": f"step_kernel<float, 9, {args.radix or 8}, RK4IP>",
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
 
     # FP32 result vs FP64 over the whole batch, full horizon
@@ -396,6 +397,8 @@ def main():
     ap.add_argument("--inner-steps", type=int, default=0,
                     help="RK4IP steps per benchmark step (default: the workload's 20000)")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--radix", type=int, default=0, help="field values per thread (0: default)")
+    ap.add_argument("--inst-per-cta", type=int, default=0, help="instances per block (0: default)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -326,7 +326,9 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         if (G == 0)
             G = P >= 64 ? 1 : std::max(1, 64 / P);
         G = std::min(G, std::max(1, 256 / P));
-        if (P < 32) {
+        if (P >= 64) {
+            G = 1;  // kernels for groups of >= 64 threads are compiled for one instance per block
+        } else if (P < 32) {
             // groups narrower than a warp synchronise with __syncwarp over full warps: make the
             // block a whole number of warps (surplus groups recompute the last instance and
             // store nothing)
@@ -486,6 +488,9 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
     a.g0 = b->g0_d + g.first;
     a.status = b->status_d + g.first;
     a.h = b->h_cur;
+    a.hf = (float)b->h_cur;
+    a.hhf = (float)(0.5 * b->h_cur);
+    a.h6f = (float)(b->h_cur / 6.0);
     return a;
 }
 

@@ -212,18 +212,20 @@ struct Xbuf<float> {
         const float2 a = p[i];
         return {a.x, a.y};
     }
+    CME_DEV Xbuf at(int off) const { return {p + off}; }
     static constexpr int words_per_elem = 1;  // in 8-byte words
 };
 template <>
 struct Xbuf<double> {
-    double* re;
-    double* im;
+    double* re;  // im = re + BUF
+    int stride;
     CME_DEV void put(int i, cx<double> v) const
     {
         re[i] = v.re;
-        im[i] = v.im;
+        re[i + stride] = v.im;
     }
-    CME_DEV cx<double> get(int i) const { return {re[i], im[i]}; }
+    CME_DEV cx<double> get(int i) const { return {re[i], re[i + stride]}; }
+    CME_DEV Xbuf at(int off) const { return {re + 2 * off, stride}; }
     static constexpr int words_per_elem = 2;
 };
 
@@ -269,42 +271,62 @@ struct Transform {
         }
     }
 
-    template <int s>
-    CME_DEV static void exchange(cx<T> (&x)[R], const Xbuf<T>& b, int t)
+    // Per-thread shared-memory addressing, computed once per launch.  With the padding
+    // p -> p + (p >> 4) every exchange address is a per-thread base plus a compile-time
+    // offset: for the write of pass s (radix R, stride L = R^s) the thread's base is
+    // b = (t - k) R + k, k = t mod L, and (b mod 16) + (jL mod 16) < 16 for all j < R, so
+    // pad(b + jL) = pad(b) + jL + (jL >> 4); likewise pad(t + jP) = pad(t) + jP + (jP >> 4).
+    struct Addr {
+        int rd;
+        int wr[NS > 1 ? NS - 1 : 1];
+    };
+    CME_DEV static Addr make_addr(int t)
     {
-        constexpr int r = PL::radix(s), Q = R / r, L = PL::L(s);
+        static_assert(R >= 4, "the padding identity needs R >= 4");
+        Addr a;
+        a.rd = PL::pad(t);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int tp = t + q * P;
-            const int k = tp & (L - 1);
-            const int base = (tp - k) * r + k;
-#pragma unroll
-            for (int j = 0; j < r; ++j)
-                b.put(PL::pad(base + j * L), x[q + j * Q]);
+        for (int s = 0; s + 1 < NS; ++s) {
+            const int L = PL::L(s);
+            const int k = t & (L - 1);
+            a.wr[s] = PL::pad((t - k) * R + k);
         }
+        return a;
+    }
+
+    template <int s>
+    CME_DEV static void exchange(cx<T> (&x)[R], const Xbuf<T>& b, const Addr& ad)
+    {
+        static_assert(PL::radix(s) == R, "exchanges follow full-radix passes");
+        constexpr int L = PL::L(s);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            b.put(ad.wr[s] + j * L + ((j * L) >> 4), x[j]);
         group_sync<WARP>();
 #pragma unroll
         for (int j = 0; j < R; ++j)
-            x[j] = b.get(PL::pad(t + j * P));
+            x[j] = b.get(ad.rd + j * P + ((j * P) >> 4));
     }
 
+    // buf: the first of two ping-pong buffers (the second starts BUF elements later); par
+    // selects the one the next exchange writes.
     template <int s, int S>
     CME_DEV static void run_from(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1],
-                                 const Xbuf<T> (&buf)[2], int& par, int t)
+                                 const Xbuf<T>& buf, int& par, const Addr& ad)
     {
         pass<s, S>(x, tw);
         if constexpr (s + 1 < NS) {
-            exchange<s>(x, buf[par], t);
+            exchange<s>(x, buf.at(par * PL::BUF), ad);
             par ^= 1;
-            run_from<s + 1, S>(x, tw, buf, par, t);
+            run_from<s + 1, S>(x, tw, buf, par, ad);
         }
     }
 
     template <int S>
     CME_DEV static void run(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1],
-                            const Xbuf<T> (&buf)[2], int& par, int t)
+                            const Xbuf<T>& buf, int& par, const Addr& ad)
     {
-        run_from<0, S>(x, tw, buf, par, t);
+        run_from<0, S>(x, tw, buf, par, ad);
     }
 
     // Twiddles exp(2 pi i j k / (L r)), k = (t + qP) mod L, from the table exp(2 pi i m/N).

@@ -28,6 +28,7 @@ struct StepArgs {
     int* status;            // per-instance status (group-relative)
     long long nsteps;
     double h;
+    float hf, hhf, h6f;     // h, h/2, h/6 rounded once to FP32 on the host
     int diag_mode;          // diagnostics kernel: DIAG_*
     void* diag_out;         // diagnostics output (same layout as the field)
 };

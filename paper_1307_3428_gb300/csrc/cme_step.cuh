@@ -6,6 +6,61 @@
 
 namespace cme {
 
+// Threads per block a kernel is compiled for: groups of P >= 64 threads run one instance per
+// block (so the register file is shared by as few threads as possible); narrower groups pack
+// up to 256 threads.
+template <int LOGN, int R>
+constexpr int max_threads() { return Plan<LOGN, R>::P >= 64 ? Plan<LOGN, R>::P : 256; }
+
+// Per-mode propagators of the RK4IP and Strang steps: E = exp(L h/2), e1 = expm1(L h/2),
+// e2 = expm1(L h).  For FP32 groups up to N = 1024 they are held in registers for the whole
+// launch; otherwise they are read through the read-only cache where used.
+template <typename T, int LOGN, int R>
+struct Props {
+    static constexpr bool IN_REGS = sizeof(T) == 4 && LOGN <= 10 && R <= 8;
+    cx<T> E[IN_REGS ? R : 1], e1[IN_REGS ? R : 1], e2[IN_REGS ? R : 1];
+    const cx<T>* pE;   // pointers pre-offset to (instance offset + t)
+    const cx<T>* pe1;
+    const cx<T>* pe2;
+
+    CME_DEV void init(const StepArgs& a, long long off, int t)
+    {
+        constexpr int P = Plan<LOGN, R>::P;
+        pE = reinterpret_cast<const cx<T>*>(a.E) + off + t;
+        pe1 = reinterpret_cast<const cx<T>*>(a.e1) + off + t;
+        pe2 = reinterpret_cast<const cx<T>*>(a.e2) + off + t;
+        if constexpr (IN_REGS) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                E[j] = gload<T>(pE, j * P);
+                e1[j] = gload<T>(pe1, j * P);
+                e2[j] = gload<T>(pe2, j * P);
+            }
+        }
+    }
+    CME_DEV cx<T> getE(int j) const
+    {
+        if constexpr (IN_REGS)
+            return E[j];
+        else
+            return gload<T>(pE, j * Plan<LOGN, R>::P);
+    }
+    CME_DEV cx<T> get1(int j) const
+    {
+        if constexpr (IN_REGS)
+            return e1[j];
+        else
+            return gload<T>(pe1, j * Plan<LOGN, R>::P);
+    }
+    CME_DEV cx<T> get2(int j) const
+    {
+        if constexpr (IN_REGS)
+            return e2[j];
+        else
+            return gload<T>(pe2, j * Plan<LOGN, R>::P);
+    }
+};
+
 // Per-thread view of one instance: the transform machinery plus the instance constants.
 template <typename T, int LOGN, int R>
 struct Group {
@@ -17,46 +72,71 @@ struct Group {
 
     int t;
     int par;
-    Xbuf<T> buf[2];
+    Xbuf<T> buf;   // first of the two ping-pong exchange buffers
+    typename TF::Addr ad;
     cx<T> tw[PL::NTW > 0 ? PL::NTW : 1];
+
+    // The step loops contain a single copy of the transform code (instruction-cache
+    // footprint): the forward transform is computed as conj(inverse(conj(x))).
+    CME_DEV void inverse(cx<T> (&x)[R]) { TF::template run<+1>(x, tw, buf, par, ad); }
 
     // F(x) = pump + i (g0/N) DFT(|a|^2 a), a = inverse transform of x   (Eq. 4)
     CME_DEV void rhs(cx<T> (&x)[R], T gN, cx<T> pump)
     {
-        TF::template run<+1>(x, tw, buf, par, t);
+#pragma unroll 1
+        for (int d = 0; d < 2; ++d) {
+            inverse(x);
+            if (d == 0) {
+                // conj(i c a) with c = (g0/N) |a|^2
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const T c = gN * (x[j].re * x[j].re + x[j].im * x[j].im);
-            x[j] = {-c * x[j].im, c * x[j].re};
+                for (int j = 0; j < R; ++j) {
+                    const T c = gN * (x[j].re * x[j].re + x[j].im * x[j].im);
+                    x[j] = {-c * x[j].im, -c * x[j].re};
+                }
+            }
         }
-        TF::template run<-1>(x, tw, buf, par, t);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            x[j].im = -x[j].im;
         if (t == 0)
             x[0] = cadd(x[0], pump);
     }
+
+    // Block-local set-up: thread index in the group, exchange buffers, addresses, twiddles.
+    CME_DEV void setup(unsigned char* smem, int g, int t_, const void* tw_table)
+    {
+        constexpr int W = Xbuf<T>::words_per_elem;  // 8-byte words per element
+        double* base = reinterpret_cast<double*>(smem) + (size_t)g * 2 * W * PL::BUF;
+        if constexpr (sizeof(T) == 4) {
+            buf.p = reinterpret_cast<float2*>(base);
+        } else {
+            buf.re = base;           // buffer 0: re [0, BUF), im [BUF, 2 BUF)
+            buf.stride = PL::BUF;    // buffer 1 starts at 2 BUF (Xbuf::at)
+        }
+        t = t_;
+        par = 0;
+        ad = TF::make_addr(t);
+        TF::load_tw(tw, tw_table, t);
+    }
 };
 
-// Set up the shared-memory exchange buffers of group g.
-template <typename T, int LOGN, int R>
-CME_DEV void setup_buffers(Group<T, LOGN, R>& grp, unsigned char* smem, int g)
-{
-    using PL = Plan<LOGN, R>;
-    constexpr int W = Xbuf<T>::words_per_elem;  // 8-byte words per element
-    constexpr int BUF = PL::BUF;
-    double* base = reinterpret_cast<double*>(smem) + (size_t)g * 2 * W * BUF;
-    if constexpr (sizeof(T) == 4) {
-        grp.buf[0].p = reinterpret_cast<float2*>(base);
-        grp.buf[1].p = reinterpret_cast<float2*>(base + BUF);
-    } else {
-        grp.buf[0].re = base;
-        grp.buf[0].im = base + BUF;
-        grp.buf[1].re = base + 2 * BUF;
-        grp.buf[1].im = base + 3 * BUF;
-    }
-}
+template <typename T>
+struct Coef;  // step coefficients in the field precision, converted once on the host
+template <>
+struct Coef<float> {
+    CME_DEV static float h(const StepArgs& a) { return a.hf; }
+    CME_DEV static float hh(const StepArgs& a) { return a.hhf; }
+    CME_DEV static float h6(const StepArgs& a) { return a.h6f; }
+};
+template <>
+struct Coef<double> {
+    CME_DEV static double h(const StepArgs& a) { return a.h; }
+    CME_DEV static double hh(const StepArgs& a) { return 0.5 * a.h; }
+    CME_DEV static double h6(const StepArgs& a) { return a.h / 6.0; }
+};
 
 template <typename T, int LOGN, int R, int METHOD>
-__global__ void __launch_bounds__((Plan<LOGN, R>::P > 256 ? Plan<LOGN, R>::P : 256))
-    step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(max_threads<LOGN, R>()) step_kernel(const StepArgs a)
 {
     using GR = Group<T, LOGN, R>;
     constexpr int N = GR::N, P = GR::P;
@@ -64,78 +144,79 @@ __global__ void __launch_bounds__((Plan<LOGN, R>::P > 256 ? Plan<LOGN, R>::P : 2
     extern __shared__ __align__(16) unsigned char smem[];
 
     const int g = threadIdx.x / P;
-    GR grp;
-    grp.t = threadIdx.x - g * P;
-    grp.par = 0;
     int inst = blockIdx.x * a.G + g;
     const bool valid = inst < a.ninst;
     if (!valid)
         inst = a.ninst - 1;  // duplicate work keeps every group in the barriers; no store
-    setup_buffers<T, LOGN, R>(grp, smem, g);
-    GR::TF::load_tw(grp.tw, a.tw, grp.t);
-
-    const long long off = a.base + (long long)inst * N;
+    GR grp;
+    grp.setup(smem, g, threadIdx.x - g * P, a.tw);
     const int t = grp.t;
+    const long long off = a.base + (long long)inst * N;
+
+    cx<T>* hi = reinterpret_cast<cx<T>*>(a.hi) + off + t;
+    cx<T>* lo = reinterpret_cast<cx<T>*>(a.lo) + off + t;
     cx<T> Dh[R], Dl[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        Dh[j] = load<T>(a.hi, off + t + j * P);
+        Dh[j] = hi[j * P];
         if constexpr (COMP)
-            Dl[j] = load<T>(a.lo, off + t + j * P);
+            Dl[j] = lo[j * P];
         else
             Dl[j] = {T(0), T(0)};
     }
     const double2 pd = a.pump[inst];
     const cx<T> pump = {(T)pd.x, (T)pd.y};
     const T gN = (T)(a.g0[inst] / (double)N);
-    const T h = (T)a.h, hh = (T)(0.5 * a.h), h6 = (T)(a.h / 6.0);
+    const T h = Coef<T>::h(a), hh = Coef<T>::hh(a), h6 = Coef<T>::h6(a);
+    Props<T, LOGN, R> pr;
+    pr.init(a, off, t);
 
     if constexpr (METHOD == METHOD_RK4IP) {
         // RK4IP (Sec. 2 "fourth-order Runge-Kutta"; Hult 2007) written as increments of D:
         //   x2 = D + (e1 D + h/2 k1),  x3 = D + (e1 D + h/2 k2),  x4 = D + (e2 D + h E k3),
         //   D' = D + e2 D + h/6 [E (k1 + 2 k2 + 2 k3) + k4],  k1 = E F(D),  k_i = F(x_i),
-        // with E = exp(L h/2), e1 = expm1(L h/2), e2 = expm1(L h).
+        // with E = exp(L h/2), e1 = expm1(L h/2), e2 = expm1(L h).  The four stages share
+        // one copy of the right-hand-side code (a runtime loop).
+        cx<T> x[R], S[R];
         for (long long n = 0; n < a.nsteps; ++n) {
-            cx<T> x[R], S[R];
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 x[j] = Dh[j];
-            grp.rhs(x, gN, pump);
+#pragma unroll 1
+            for (int st = 0; st < 4; ++st) {
+                grp.rhs(x, gN, pump);
+                if (st == 0) {
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const long long m = off + t + j * P;
-                const cx<T> E = gload<T>(a.E, m), e1 = gload<T>(a.e1, m);
-                const cx<T> k1 = cmul(E, x[j]);
-                S[j] = cmul(E, k1);
-                x[j] = cadd(Dh[j], caxpy(cmul(e1, Dh[j]), hh, k1));
-            }
-            grp.rhs(x, gN, pump);
+                    for (int j = 0; j < R; ++j) {
+                        const cx<T> E = pr.getE(j);
+                        const cx<T> k1 = cmul(E, x[j]);
+                        S[j] = cmul(E, k1);
+                        x[j] = cadd(Dh[j], caxpy(cmul(pr.get1(j), Dh[j]), hh, k1));
+                    }
+                } else if (st == 1) {
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const long long m = off + t + j * P;
-                const cx<T> E = gload<T>(a.E, m), e1 = gload<T>(a.e1, m);
-                S[j] = caxpy(S[j], T(2), cmul(E, x[j]));
-                x[j] = cadd(Dh[j], caxpy(cmul(e1, Dh[j]), hh, x[j]));
-            }
-            grp.rhs(x, gN, pump);
+                    for (int j = 0; j < R; ++j) {
+                        S[j] = caxpy(S[j], T(2), cmul(pr.getE(j), x[j]));
+                        x[j] = cadd(Dh[j], caxpy(cmul(pr.get1(j), Dh[j]), hh, x[j]));
+                    }
+                } else if (st == 2) {
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const long long m = off + t + j * P;
-                const cx<T> E = gload<T>(a.E, m), e2 = gload<T>(a.e2, m);
-                const cx<T> Ek3 = cmul(E, x[j]);
-                S[j] = caxpy(S[j], T(2), Ek3);
-                x[j] = cadd(Dh[j], caxpy(cmul(e2, Dh[j]), h, Ek3));
-            }
-            grp.rhs(x, gN, pump);
+                    for (int j = 0; j < R; ++j) {
+                        const cx<T> Ek3 = cmul(pr.getE(j), x[j]);
+                        S[j] = caxpy(S[j], T(2), Ek3);
+                        x[j] = cadd(Dh[j], caxpy(cmul(pr.get2(j), Dh[j]), h, Ek3));
+                    }
+                } else {
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const long long m = off + t + j * P;
-                const cx<T> e2 = gload<T>(a.e2, m);
-                cx<T> d = cmul(e2, Dh[j]);
-                if constexpr (COMP)
-                    d = cadd(d, cmul(e2, Dl[j]));
-                d = caxpy(d, h6, cadd(S[j], x[j]));
-                accumulate<T, COMP>(Dh[j], Dl[j], d);
+                    for (int j = 0; j < R; ++j) {
+                        const cx<T> e2 = pr.get2(j);
+                        cx<T> d = cmul(e2, Dh[j]);
+                        if constexpr (COMP)
+                            d = cadd(d, cmul(e2, Dl[j]));
+                        d = caxpy(d, h6, cadd(S[j], x[j]));
+                        accumulate<T, COMP>(Dh[j], Dl[j], d);
+                    }
+                }
             }
         }
     } else {
@@ -148,36 +229,41 @@ __global__ void __launch_bounds__((Plan<LOGN, R>::P > 256 ? Plan<LOGN, R>::P : 2
         const T g0h = (T)(a.g0[inst] * a.h * 0.5);   // half Kerr phase per |a|^2
         const T invN = (T)(1.0 / N);
         for (long long n = 0; n < a.nsteps; ++n) {
-#pragma unroll
+#pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 if (half == 1) {
                     cx<T> x[R];
 #pragma unroll
                     for (int j = 0; j < R; ++j)
                         x[j] = Dh[j];
-                    GR::TF::template run<+1>(x, grp.tw, grp.buf, grp.par, t);
+#pragma unroll 1
+                    for (int d = 0; d < 2; ++d) {
+                        grp.inverse(x);
+                        if (d == 0) {
 #pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h
-                        const T ph2 = g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
-                        T s, c;
-                        if constexpr (sizeof(T) == 4)
-                            sincosf(ph2, &s, &c);
-                        else
-                            sincos(ph2, &s, &c);
-                        const cx<T> em = {T(-2) * s * s * invN, T(2) * s * c * invN};
-                        x[j] = cmul(x[j], em);
+                            for (int j = 0; j < R; ++j) {
+                                // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h;
+                                // the forward transform runs as conj(inverse(conj(.)))
+                                const T ph2 = g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
+                                T s, c;
+                                if constexpr (sizeof(T) == 4)
+                                    sincosf(ph2, &s, &c);
+                                else
+                                    sincos(ph2, &s, &c);
+                                const cx<T> em = {T(-2) * s * s * invN, T(2) * s * c * invN};
+                                const cx<T> b = cmul(x[j], em);
+                                x[j] = {b.re, -b.im};
+                            }
+                        }
                     }
-                    GR::TF::template run<-1>(x, grp.tw, grp.buf, grp.par, t);
 #pragma unroll
                     for (int j = 0; j < R; ++j)
-                        accumulate<T, COMP>(Dh[j], Dl[j], x[j]);
+                        accumulate<T, COMP>(Dh[j], Dl[j], cx<T>{x[j].re, -x[j].im});
                 }
                 // linear + pump half step: D += e1 D + delta_{mu,0} c
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    const long long m = off + t + j * P;
-                    const cx<T> e1 = gload<T>(a.e1, m);
+                    const cx<T> e1 = pr.get1(j);
                     cx<T> d = cmul(e1, Dh[j]);
                     if constexpr (COMP)
                         d = cadd(d, cmul(e1, Dl[j]));
@@ -196,9 +282,9 @@ __global__ void __launch_bounds__((Plan<LOGN, R>::P > 256 ? Plan<LOGN, R>::P : 2
     if (valid) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            store<T>(a.hi, off + t + j * P, Dh[j]);
+            hi[j * P] = Dh[j];
             if constexpr (COMP)
-                store<T>(a.lo, off + t + j * P, Dl[j]);
+                lo[j * P] = Dl[j];
         }
         if (bad)
             a.status[inst] = 1;
@@ -208,32 +294,30 @@ __global__ void __launch_bounds__((Plan<LOGN, R>::P > 256 ? Plan<LOGN, R>::P : 2
 // Diagnostics: one transform or one right-hand-side evaluation of the current field, written in
 // transform order to a.diag_out (same layout as the field).
 template <typename T, int LOGN, int R>
-__global__ void __launch_bounds__((Plan<LOGN, R>::P > 256 ? Plan<LOGN, R>::P : 256))
-    diag_kernel(const StepArgs a)
+__global__ void __launch_bounds__(max_threads<LOGN, R>()) diag_kernel(const StepArgs a)
 {
     using GR = Group<T, LOGN, R>;
     constexpr int N = GR::N, P = GR::P;
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = threadIdx.x / P;
-    GR grp;
-    grp.t = threadIdx.x - g * P;
-    grp.par = 0;
     int inst = blockIdx.x * a.G + g;
     const bool valid = inst < a.ninst;
     if (!valid)
         inst = a.ninst - 1;
-    setup_buffers<T, LOGN, R>(grp, smem, g);
-    GR::TF::load_tw(grp.tw, a.tw, grp.t);
-    const long long off = a.base + (long long)inst * N;
+    GR grp;
+    grp.setup(smem, g, threadIdx.x - g * P, a.tw);
     const int t = grp.t;
+    const long long off = a.base + (long long)inst * N;
+    const cx<T>* src = reinterpret_cast<const cx<T>*>(a.hi) + off + t;
+    cx<T>* dst = reinterpret_cast<cx<T>*>(a.diag_out) + off + t;
     cx<T> x[R];
 #pragma unroll
     for (int j = 0; j < R; ++j)
-        x[j] = load<T>(a.hi, off + t + j * P);
+        x[j] = src[j * P];
     if (a.diag_mode == DIAG_IDFT) {
-        GR::TF::template run<+1>(x, grp.tw, grp.buf, grp.par, t);
+        GR::TF::template run<+1>(x, grp.tw, grp.buf, grp.par, grp.ad);
     } else if (a.diag_mode == DIAG_DFT) {
-        GR::TF::template run<-1>(x, grp.tw, grp.buf, grp.par, t);
+        GR::TF::template run<-1>(x, grp.tw, grp.buf, grp.par, grp.ad);
     } else {
         const double2 pd = a.pump[inst];
         grp.rhs(x, (T)(a.g0[inst] / (double)N), cx<T>{(T)pd.x, (T)pd.y});
@@ -241,7 +325,7 @@ __global__ void __launch_bounds__((Plan<LOGN, R>::P > 256 ? Plan<LOGN, R>::P : 2
     if (valid) {
 #pragma unroll
         for (int j = 0; j < R; ++j)
-            store<T>(a.diag_out, off + t + j * P, x[j]);
+            dst[j * P] = x[j];
     }
 }
 
