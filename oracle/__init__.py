@@ -63,8 +63,16 @@ def _load():
                                                  c_double, c_long, dp]
             lib.oracle_dft.argtypes = [c_int, c_int, dp, dp]
             lib.oracle_invariants.argtypes = [c_int, c_int, dp, c_double, c_double, dp, dp]
+            lib.oracle_rk4ip_grad.argtypes = [c_int, c_int, dp, dp, c_double, c_double, c_double,
+                                              c_double, c_double, c_double, c_long, dp, dp,
+                                              c_double, dp, dp, dp, dp, dp]
+            lib.oracle_rk4ip_loss.argtypes = [c_int, c_int, dp, dp, c_double, c_double, c_double,
+                                              c_double, c_double, c_double, c_long, dp, dp,
+                                              c_double, dp]
+            lib.oracle_fwm_vjp.argtypes = [c_int, c_int, dp, dp, dp]
             for name in ("oracle_fwm", "oracle_rhs", "oracle_integrate", "oracle_integrate_eq1",
-                         "oracle_dft", "oracle_invariants"):
+                         "oracle_dft", "oracle_invariants", "oracle_rk4ip_grad",
+                         "oracle_rk4ip_loss", "oracle_fwm_vjp"):
                 getattr(lib, name).restype = c_int
             _lib = lib
     return _lib
@@ -146,6 +154,67 @@ def invariants(D, omega, g0: float, sigma: float, linear: bool = False):
     out = np.empty(2)
     _check(_load().oracle_invariants(N, int(linear), _dp(om), g0, sigma, _dp(d), _dp(out)))
     return float(out[0]), float(out[1])
+
+
+def fwm_vjp(D, Wbar, linear: bool = False) -> np.ndarray:
+    """J^H Wbar of the direct FWM sum at D (cotangent convention dL/dRe + i dL/dIm)."""
+    d = _cbuf(D)
+    wb = _cbuf(Wbar)
+    N = d.size // 2
+    out = np.empty_like(d)
+    _check(_load().oracle_fwm_vjp(N, int(linear), _dp(d), _dp(wb), _dp(out)))
+    return out.view(np.complex128)
+
+
+def log_spectrum_loss(inst, h: float, nsteps: int, target, eps: float = 1e-20,
+                      linear: bool = False, D0=None) -> float:
+    """L = sum_mu (log10(|D_mu|^2 + eps) - T_mu)^2 after nsteps RK4IP steps."""
+    d = _cbuf(inst.D0 if D0 is None else D0)
+    kap = np.ascontiguousarray(inst.kappa, dtype=np.float64)
+    om = np.ascontiguousarray(inst.omega, dtype=np.float64)
+    T = np.ascontiguousarray(target, dtype=np.float64)
+    A = complex(inst.A_in)
+    out = np.zeros(1)
+    _check(_load().oracle_rk4ip_loss(inst.N, int(linear), _dp(kap), _dp(om), inst.g0,
+                                     inst.kappa_ext, A.real, A.imag, inst.sigma, h, int(nsteps),
+                                     _dp(d), _dp(T), eps, _dp(out)))
+    return float(out[0])
+
+
+def log_spectrum_grad(inst, h: float, nsteps: int, target, eps: float = 1e-20,
+                      linear: bool = False):
+    """Discrete adjoint of the RK4IP run for the log-spectrum loss.  Returns a dict with the
+    loss and the gradients with respect to the initial field (complex, dL/dRe + i dL/dIm),
+    sigma, the omega_mu array, the kappa_mu array, A_in (complex) and, for
+    omega_mu = D2 mu^2/2 + D3 mu^3/6, D2 and D3."""
+    N = inst.N
+    d = _cbuf(inst.D0)
+    kap = np.ascontiguousarray(inst.kappa, dtype=np.float64)
+    om = np.ascontiguousarray(inst.omega, dtype=np.float64)
+    T = np.ascontiguousarray(target, dtype=np.float64)
+    A = complex(inst.A_in)
+    loss = np.zeros(1)
+    gD0 = np.zeros(2 * N)
+    gLi = np.zeros(N)
+    gLr = np.zeros(N)
+    gP = np.zeros(2)
+    _check(_load().oracle_rk4ip_grad(N, int(linear), _dp(kap), _dp(om), inst.g0, inst.kappa_ext,
+                                     A.real, A.imag, inst.sigma, h, int(nsteps), _dp(d), _dp(T),
+                                     eps, _dp(loss), _dp(gD0), _dp(gLi), _dp(gLr), _dp(gP)))
+    mu = np.arange(N) - N // 2
+    # Im L_mu = omega_mu - omega_0 - sigma; Re L_mu = -kappa_mu / 2
+    g_omega = gLi.copy()
+    g_omega[N // 2] -= gLi.sum()
+    return {
+        "loss": float(loss[0]),
+        "D0": gD0.view(np.complex128),
+        "sigma": float(-gLi.sum()),
+        "omega": g_omega,
+        "kappa": -0.5 * gLr,
+        "A_in": complex(gP[0], gP[1]) * np.sqrt(inst.kappa_ext),
+        "D2": float(np.sum(g_omega * mu * mu / 2.0)),
+        "D3": float(np.sum(g_omega * mu ** 3 / 6.0)),
+    }
 
 
 def to_lab_frame(inst, D, tau: float) -> np.ndarray:

@@ -394,3 +394,206 @@ int oracle_invariants(int N, int linear, const double* omega, double g0, double 
     free(d);
     return ORACLE_OK;
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Discrete adjoint of the RK4IP map (reverse mode through exactly the steps of step_rk4ip),
+ * for the log-power-spectrum misfit loss
+ *     L = sum_mu (log10(|D_mu|^2 + eps) - T_mu)^2     at the final step.
+ * Cotangents of complex quantities follow vbar = dL/dRe v + i dL/dIm v, so that for y = a x
+ * (complex product) xbar += conj(a) ybar and abar += conj(x) ybar.
+ *
+ * VJP of the FWM sum, from its definition FWM_mu = sum_{beta,gamma} D_{mu+beta-gamma}
+ * conj(D_beta) D_gamma (indices modulo N or linear):
+ *     Dbar_nu = 2 sum_{mu,beta} Wbar_mu D_beta conj(D_{mu+beta-nu})
+ *             +   sum_{mu,gamma} conj(Wbar_mu) D_{mu+nu-gamma} D_gamma .
+ * Outputs: gD0 (cotangent of the initial field), gLi / gLr (dL/dIm L_mu and dL/dRe L_mu summed
+ * over all steps, L_mu = -kappa_mu/2 + i(omega_mu - omega_0 - sigma)) and gP (cotangent of the
+ * pump sqrt(kappa_ext) A_in).
+ * ------------------------------------------------------------------------------------- */
+static int idx_of(long alpha, int N, int linear)
+{
+    const int h = N / 2;
+    if (linear) {
+        if (alpha < -h || alpha >= N - h)
+            return -1;
+        return (int)(alpha + h);
+    }
+    return wrap_index(alpha, N);
+}
+
+static void fwm_vjp(int N, int linear, const cplx* D, const cplx* Wbar, cplx* Dbar)
+{
+    const int h = N / 2;
+    for (int nu = -h; nu < N - h; ++nu) {
+        cplx s = 0.0;
+        for (int mu = -h; mu < N - h; ++mu) {
+            const cplx w = Wbar[mu + h];
+            for (int beta = -h; beta < N - h; ++beta) {
+                const int i = idx_of((long)mu + beta - nu, N, linear);
+                if (i >= 0)
+                    s += 2.0 * w * D[beta + h] * conj(D[i]);
+            }
+            for (int gamma = -h; gamma < N - h; ++gamma) {
+                const int i = idx_of((long)mu + nu - gamma, N, linear);
+                if (i >= 0)
+                    s += conj(w) * D[i] * D[gamma + h];
+            }
+        }
+        Dbar[nu + h] = s;
+    }
+}
+
+/* xbar += J_F(x)^H ybar for F(x) = pump + i g0 FWM(x); pbar += ybar at mu = 0. */
+static void rhs_vjp(const model* m, const cplx* x, const cplx* ybar, cplx* xbar, cplx* pbar,
+                    cplx* tmp)
+{
+    const int N = m->N;
+    for (int i = 0; i < N; ++i)
+        tmp[i] = conj(I * m->g0) * ybar[i];
+    fwm_vjp(N, m->linear, x, tmp, tmp + N);
+    for (int i = 0; i < N; ++i)
+        xbar[i] += tmp[N + i];
+    *pbar += ybar[N / 2];
+}
+
+int oracle_rk4ip_grad(int N, int linear, const double* kappa, const double* omega, double g0,
+                      double kappa_ext, double ain_re, double ain_im, double sigma, double h,
+                      long nsteps, const double* D0, const double* target, double eps,
+                      double* loss, double* gD0, double* gLi, double* gLr, double* gP)
+{
+    if (check_model(N, kappa, omega) || !D0 || !target || nsteps < 0 || !loss)
+        return ORACLE_EINVAL;
+    model m = {N, linear, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    cplx* traj = malloc(sizeof(cplx) * N * (size_t)(nsteps + 1));
+    cplx* w = malloc(sizeof(cplx) * 24 * N);
+    cplx *E = w, *y1 = w + N, *k1 = w + 2 * N, *k2 = w + 3 * N, *k3 = w + 4 * N,
+         *k4 = w + 5 * N, *u = w + 6 * N, *x2 = w + 7 * N, *x3 = w + 8 * N, *v = w + 9 * N,
+         *x4 = w + 10 * N, *ww = w + 11 * N, *Db = w + 12 * N, *Dp = w + 13 * N,
+         *wb = w + 14 * N, *xb = w + 15 * N, *vb = w + 16 * N, *ub = w + 17 * N,
+         *kb = w + 18 * N, *Eb = w + 19 * N, *tmp = w + 20 * N; /* tmp uses 2N */
+    load(N, D0, traj);
+    cplx* sw = malloc(sizeof(cplx) * 8 * N);
+    for (long n = 0; n < nsteps; ++n) {
+        memcpy(traj + (size_t)(n + 1) * N, traj + (size_t)n * N, sizeof(cplx) * N);
+        step_rk4ip(&m, h, traj + (size_t)(n + 1) * N, sw);
+    }
+    free(sw);
+    /* loss and its seed */
+    const cplx* Df = traj + (size_t)nsteps * N;
+    double L = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double P = creal(Df[i]) * creal(Df[i]) + cimag(Df[i]) * cimag(Df[i]);
+        const double r = log10(P + eps) - target[i];
+        L += r * r;
+        const double dLdP = 2.0 * r / ((P + eps) * log(10.0));
+        Db[i] = 2.0 * dLdP * Df[i];
+    }
+    *loss = L;
+    for (int i = 0; i < N; ++i) {
+        E[i] = cexp(lin_coef(&m, i) * (0.5 * h));
+        gLi[i] = 0.0;
+        gLr[i] = 0.0;
+    }
+    cplx pbar = 0.0;
+    for (long n = nsteps - 1; n >= 0; --n) {
+        const cplx* D = traj + (size_t)n * N;
+        /* forward stages of step n */
+        rhs_nonlinear(&m, D, y1);
+        for (int i = 0; i < N; ++i) {
+            k1[i] = E[i] * y1[i];
+            u[i] = E[i] * D[i];
+            x2[i] = u[i] + 0.5 * h * k1[i];
+        }
+        rhs_nonlinear(&m, x2, k2);
+        for (int i = 0; i < N; ++i)
+            x3[i] = u[i] + 0.5 * h * k2[i];
+        rhs_nonlinear(&m, x3, k3);
+        for (int i = 0; i < N; ++i) {
+            v[i] = u[i] + h * k3[i];
+            x4[i] = E[i] * v[i];
+            ww[i] = u[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i]);
+        }
+        (void)k4;
+        /* reverse: Db holds the cotangent of D_{n+1} */
+        for (int i = 0; i < N; ++i) {
+            wb[i] = conj(E[i]) * Db[i];
+            Eb[i] = conj(ww[i]) * Db[i];
+            kb[i] = h / 6.0 * Db[i]; /* k4bar */
+            xb[i] = 0.0;
+        }
+        rhs_vjp(&m, x4, kb, xb, &pbar, tmp); /* xb = x4bar */
+        for (int i = 0; i < N; ++i) {
+            vb[i] = conj(E[i]) * xb[i];
+            Eb[i] += conj(v[i]) * xb[i];
+            ub[i] = wb[i] + vb[i];
+            kb[i] = h / 3.0 * wb[i] + h * vb[i]; /* k3bar */
+            xb[i] = 0.0;
+        }
+        rhs_vjp(&m, x3, kb, xb, &pbar, tmp); /* x3bar */
+        for (int i = 0; i < N; ++i) {
+            ub[i] += xb[i];
+            kb[i] = h / 3.0 * wb[i] + 0.5 * h * xb[i]; /* k2bar */
+            xb[i] = 0.0;
+        }
+        rhs_vjp(&m, x2, kb, xb, &pbar, tmp); /* x2bar */
+        for (int i = 0; i < N; ++i) {
+            ub[i] += xb[i];
+            kb[i] = h / 6.0 * wb[i] + 0.5 * h * xb[i]; /* k1bar */
+            Dp[i] = conj(E[i]) * ub[i];
+            Eb[i] += conj(D[i]) * ub[i];
+            xb[i] = conj(E[i]) * kb[i]; /* y1bar */
+            Eb[i] += conj(y1[i]) * kb[i];
+        }
+        rhs_vjp(&m, D, xb, Dp, &pbar, tmp);
+        for (int i = 0; i < N; ++i) {
+            /* E = exp(L h/2): Lbar = conj(h/2 E) Ebar */
+            const cplx Lb = conj(0.5 * h * E[i]) * Eb[i];
+            gLr[i] += creal(Lb);
+            gLi[i] += cimag(Lb);
+            Db[i] = Dp[i];
+        }
+    }
+    store(N, Db, gD0);
+    gP[0] = creal(pbar);
+    gP[1] = cimag(pbar);
+    free(traj);
+    free(w);
+    return ORACLE_OK;
+}
+
+/* Loss of the forward RK4IP run alone (for finite differences). */
+int oracle_rk4ip_loss(int N, int linear, const double* kappa, const double* omega, double g0,
+                      double kappa_ext, double ain_re, double ain_im, double sigma, double h,
+                      long nsteps, const double* D0, const double* target, double eps,
+                      double* loss)
+{
+    if (check_model(N, kappa, omega) || !D0 || !target || !loss)
+        return ORACLE_EINVAL;
+    double* d = malloc(sizeof(double) * 2 * N);
+    memcpy(d, D0, sizeof(double) * 2 * N);
+    int rc = oracle_integrate(0, N, linear, kappa, omega, g0, kappa_ext, ain_re, ain_im, sigma, h,
+                              nsteps, d);
+    double L = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double P = d[2 * i] * d[2 * i] + d[2 * i + 1] * d[2 * i + 1];
+        const double r = log10(P + eps) - target[i];
+        L += r * r;
+    }
+    *loss = L;
+    free(d);
+    return rc;
+}
+
+/* J^H w for the FWM map at D (exposed for the dot-product test). */
+int oracle_fwm_vjp(int N, int linear, const double* D, const double* Wbar, double* Dbar)
+{
+    if (N < 1 || !D || !Wbar || !Dbar)
+        return ORACLE_EINVAL;
+    cplx* d = malloc(sizeof(cplx) * 3 * N);
+    load(N, D, d);
+    load(N, Wbar, d + N);
+    fwm_vjp(N, linear, d, d + N, d + 2 * N);
+    store(N, d + 2 * N, Dbar);
+    free(d);
+    return ORACLE_OK;
+}
