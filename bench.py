@@ -41,6 +41,7 @@ UNIT = "mode-steps/s"
 SMS = 152
 FP32_LANES = 128          # FP32 FMA lanes per SM
 SM_MAX_MHZ = 2070.0       # maximum SM clock of the part
+FP64_NOMINAL_TFLOPS = 1.25
 KERNEL_SOURCES = ["cme_core.cuh", "cme_step.cuh", "cme_launch.cuh", "kern_fp32_rk4ip.cu"]
 
 
@@ -213,15 +214,29 @@ def run_gpu(args, world, rank, local):
     from paper_1307_3428_gb300 import workloads as wl
 
     torch.cuda.set_device(local)
-    w = wl.sweep512(seed_offset=256 * rank) if rank else wl.sweep512()
-    N = 512
+    if args.workload == "sweep512":
+        w = wl.sweep512(seed_offset=256 * rank) if rank else wl.sweep512()
+    elif args.workload == "uneven":
+        w = wl.uneven()
+    elif args.workload == "plain64":
+        w = wl.plain64()
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    headline = args.workload == "sweep512"
+    sizes = [i.N for i in w.instances]
+    N = max(sizes)
     count = len(w.instances)
     nsteps = args.inner_steps or w.nsteps
-    mode_steps = count * N * nsteps
+    mode_steps = sum(sizes) * nsteps
 
     insts = [cme.Instance.from_workload(i) for i in w.instances]
-    b32 = cme.Batch(insts, precision=cme.FP32, use_graph=True, radix=args.radix,
-                    inst_per_cta=args.inst_per_cta)
+    prec_main = cme.FP64 if args.workload == "plain64" else cme.FP32
+    b32 = cme.Batch(insts, precision=prec_main, use_graph=True, radix=args.radix,
+                    inst_per_cta=args.inst_per_cta, persistent=args.persistent,
+                    integrator=cme.STRANG if args.strang else cme.RK4IP)
+    plan = None
+    if args.autotune:
+        plan = b32.autotune(w.h, probe_steps=200)
     stream = torch.cuda.ExternalStream(b32.stream)
     D0 = np.concatenate([i.D0 for i in w.instances])
     d0_dev = torch.from_numpy(D0.view(np.float64).copy()).cuda()
@@ -268,7 +283,9 @@ def run_gpu(args, world, rank, local):
 
     # roofline of the step kernel (one graph node per replay)
     kern_ms = statistics.mean(k_ms)
-    flops = mode_steps * flops_per_mode_step(N)
+    flops = sum(n * flops_per_mode_step(n) for n in sizes) * nsteps
+    if args.strang:
+        flops = sum(n * (10.0 * math.log2(n) + 40.0) for n in sizes) * nsteps
     achieved = flops / (kern_ms * 1e-3) / 1e12
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     traffic = None
@@ -279,16 +296,21 @@ def run_gpu(args, world, rank, local):
         ent = tj.get("step_kernel_fp32_n512")
         if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("steps") == nsteps:
             traffic = ent.get("dram_bytes_per_launch")
+    if prec_main == cme.FP64:
+        peak = FP64_NOMINAL_TFLOPS
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"step_kernel<float, 9, {args.radix or 8}, RK4IP>",
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
+                "kernel": (f"step_kernel<float, 9, {args.radix or 8}, RK4IP>" if headline
+                           else f"{args.workload} step kernel(s)"),
+                "peak_basis": ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"
+                               if prec_main == cme.FP32 else "GB300 nominal FP64 1.25 TFLOP/s")}
 
     # FP32 result vs FP64 over the whole batch, full horizon
     fin32 = b32.get_state()
-    b64 = cme.Batch(insts, precision=cme.FP64, use_graph=True)
     fp64 = {}
-    if not args.skip_fp64:
+    error = {}
+    if headline and not args.skip_fp64:
+        b64 = cme.Batch(insts, precision=cme.FP64, use_graph=True)
         one_step(b64)                                 # warm-up / graph build
         torch.cuda.synchronize()
         s64 = torch.cuda.ExternalStream(b64.stream)
@@ -330,13 +352,11 @@ def run_gpu(args, world, rank, local):
         }
         error = {"fp32_vs_fp64_rel_l2_max": max(errs), "fp32_vs_fp64_rel_l2_median":
                  statistics.median(errs), "instances": len(errs), "bound_fp32": 1e-4}
-    else:
-        error = {}
 
     # end to end through the C ABI with host buffers
     pinned_in = torch.from_numpy(D0.view(np.float64).copy()).pin_memory()
     host_in = pinned_in.numpy()
-    spec = torch.empty(count * N, dtype=torch.float64).pin_memory().numpy()
+    spec = torch.empty(sum(sizes), dtype=torch.float64).pin_memory().numpy()
     import ctypes
     lib = cme.load()
     dp = ctypes.POINTER(ctypes.c_double)
@@ -356,9 +376,11 @@ def run_gpu(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"sweep_n512_b256: N=512 x {count} instances per GPU, sigma "
-                               f"-2..10, A_in=2.5, D2=0.02, {nsteps} RK4IP steps of h=5e-4, "
-                               "FP32 field with FP64-derived propagators, one CUDA graph",
+        "config": {"workload": (f"sweep_n512_b256: N=512 x {count} instances per GPU, sigma "
+                                f"-2..10, A_in=2.5, D2=0.02, {nsteps} RK4IP steps of h=5e-4, "
+                                "FP32 field with FP64-derived propagators, one CUDA graph")
+                   if headline else f"{w.name}: {w.description}, {nsteps} steps, "
+                                    f"{count} instances",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}", "global_instances": world * count},
         "roofline": roofline,
@@ -369,8 +391,12 @@ def run_gpu(args, world, rank, local):
         "error": error,
         "wall_s_timed": wall,
     }
+    if plan is not None:
+        line["config"]["plan"] = plan
+    if not headline:
+        line["dtype"] = "f64" if prec_main == cme.FP64 else "f32"
 
-    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+    if headline and rank == 0 and world == 1 and not args.skip_cpu_baseline:
         rate, steps, dt, Dref = oracle_sample(args.ref_seconds)
         # the GPU on exactly the oracle's sample
         one = cme.Batch([insts[128]], precision=cme.FP32)
@@ -399,6 +425,11 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--radix", type=int, default=0, help="field values per thread (0: default)")
     ap.add_argument("--inst-per-cta", type=int, default=0, help="instances per block (0: default)")
+    ap.add_argument("--workload", default="sweep512", choices=["sweep512", "uneven", "plain64"],
+                    help="sweep512 is the headline workload; the others are secondary records")
+    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--strang", action="store_true", help="Strang split step instead of RK4IP")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -69,6 +69,9 @@ typedef struct cme_options {
     int inst_per_cta;      /* instances sharing one thread block; 0 = library choice */
     long steps_per_launch; /* steps per kernel launch; 0 = all steps of a call in one launch */
     int use_graph;         /* 1 = cme_step replays a cached CUDA graph per (h, nsteps) */
+    int persistent;        /* batches with several N: 0 = library choice, 1 = one kernel per
+                              N group (concurrent streams), 2 = one persistent work-list
+                              kernel for all groups */
 } cme_options;
 
 /* Fill *opt with the defaults: CME_FP64, CME_RK4IP, library-chosen launch shape, no graph. */
@@ -116,6 +119,13 @@ void* cme_batch_stream(cme_batch b);
  * expm1(L h) in FP64.  nsteps = 0 is a no-op.  Errors: INVALID_ARG, CUDA. */
 int cme_step(cme_batch b, double h, long nsteps);
 
+/* Pick the fastest launch plan for this batch and step size h by timing `probe_steps` steps of
+ * each candidate (values per thread, instances per block, per-group vs persistent launch) on
+ * the device; the field is saved before and restored after, so the batch state is unchanged.
+ * The chosen plan replaces the batch's options for later cme_step calls; *plan_out (may be
+ * NULL) receives it.  Synchronises.  Errors: INVALID_ARG, CUDA. */
+int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out);
+
 /* Wait for the batch's stream; returns CME_ERR_NONFINITE if any instance's status is set. */
 int cme_synchronize(cme_batch b);
 
@@ -143,6 +153,33 @@ int cme_set_time(cme_batch b, double tau);
 /* Per-instance status words (host array of `count` ints): 0 = finite, 1 = non-finite value
  * seen at the end of a launch.  Synchronises. */
 int cme_status(cme_batch b, int* per_instance);
+
+/* ---- gradients (discrete adjoint) ------------------------------------------------------- */
+
+/* Gradients of the log-power-spectrum misfit at the final step, per instance
+ *     L = sum_mu (log10(|D_mu|^2 + eps) - T_mu)^2 ,
+ * through nsteps RK4IP steps of size h (the paper's integrator, Sec. 2).  Every pointer is a
+ * host array and may be NULL to skip that output; complex cotangents are dL/dRe + i dL/dIm,
+ * interleaved; per-mode arrays are centred. */
+typedef struct cme_grads {
+    double* loss;    /* [count] L of each instance */
+    double* d_sigma; /* [count] dL/dsigma */
+    double* d_A_in;  /* [2*count] dL/dRe A_in + i dL/dIm A_in */
+    double* d_D2;    /* [count] sum_mu dL/domega_mu mu^2/2 (omega_mu = D2 mu^2/2 + D3 mu^3/6) */
+    double* d_D3;    /* [count] sum_mu dL/domega_mu mu^3/6 */
+    double* d_omega; /* [total_modes] dL/domega_mu */
+    double* d_kappa; /* [total_modes] dL/dkappa_mu */
+    double* d_D0;    /* [2*total_modes] cotangent of the field at the start of the call */
+} cme_grads;
+
+/* Run nsteps RK4IP steps from the current field with checkpoints every `segment` steps (0 =
+ * ceil(sqrt(nsteps))), evaluate L against the target T (total_modes doubles: log10 powers,
+ * centred, host memory), then run the discrete adjoint backwards, recomputing each segment from
+ * its checkpoint.  The batch ends at the final field (tau advanced by h nsteps).  Scratch
+ * memory (checkpoints, one segment of states, stage values) is allocated on the first call and
+ * kept with the batch.  RK4IP batches only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM. */
+int cme_grad(cme_batch b, double h, long nsteps, const double* target, double eps, long segment,
+             cme_grads* out);
 
 /* ---- hot-path pieces, for testing ----------------------------------------------------- */
 

@@ -43,7 +43,13 @@ class CmeError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("integrator", ctypes.c_int),
                 ("radix", ctypes.c_int), ("inst_per_cta", ctypes.c_int),
-                ("steps_per_launch", ctypes.c_long), ("use_graph", ctypes.c_int)]
+                ("steps_per_launch", ctypes.c_long), ("use_graph", ctypes.c_int),
+                ("persistent", ctypes.c_int)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [(n, ctypes.POINTER(ctypes.c_double)) for n in
+                ("loss", "d_sigma", "d_A_in", "d_D2", "d_D3", "d_omega", "d_kappa", "d_D0")]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -67,6 +73,7 @@ _SIGS = [
     ("cme_batch_stream", _VP, [_VP]),
     ("cme_step", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long]),
     ("cme_synchronize", ctypes.c_int, [_VP]),
+    ("cme_autotune", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long, ctypes.POINTER(Options)]),
     ("cme_spectrum", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
     ("cme_get_state", ctypes.c_int, [_VP, _DP, ctypes.c_int]),
     ("cme_set_state", ctypes.c_int, [_VP, _DP, ctypes.c_int]),
@@ -76,6 +83,8 @@ _SIGS = [
     ("cme_get_time", ctypes.c_int, [_VP, _DP]),
     ("cme_set_time", ctypes.c_int, [_VP, ctypes.c_double]),
     ("cme_status", ctypes.c_int, [_VP, _IP]),
+    ("cme_grad", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long, _DP, ctypes.c_double,
+                                ctypes.c_long, ctypes.POINTER(Grads)]),
     ("cme_transform", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int]),
     ("cme_eval_rhs", ctypes.c_int, [_VP, _DP, ctypes.c_int]),
     ("cme_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, _VP]),
@@ -178,7 +187,8 @@ class Batch:
     """Device-resident batch of instances (see cme_batch_create)."""
 
     def __init__(self, instances: Sequence, precision=FP64, integrator=RK4IP, radix=0,
-                 inst_per_cta=0, steps_per_launch=0, use_graph=False, stream=None):
+                 inst_per_cta=0, steps_per_launch=0, use_graph=False, stream=None,
+                 persistent=0):
         lib = load()
         insts = [i if isinstance(i, Instance) else Instance.from_workload(i) for i in instances]
         opt = Options()
@@ -186,6 +196,7 @@ class Batch:
         opt.precision, opt.integrator = int(precision), int(integrator)
         opt.radix, opt.inst_per_cta = int(radix), int(inst_per_cta)
         opt.steps_per_launch, opt.use_graph = int(steps_per_launch), int(bool(use_graph))
+        opt.persistent = int(persistent)
         arr = (ctypes.c_void_p * len(insts))(*[i.handle.value for i in insts])
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(stream) if stream else None
@@ -215,6 +226,11 @@ class Batch:
 
     def synchronize(self):
         _check(load().cme_synchronize(self.handle))
+
+    def autotune(self, h: float, probe_steps: int = 200) -> dict:
+        opt = Options()
+        _check(load().cme_autotune(self.handle, float(h), int(probe_steps), ctypes.byref(opt)))
+        return {f: getattr(opt, f) for f, _ in Options._fields_}
 
     def split(self, flat: np.ndarray):
         return [flat[self.offsets[i]:self.offsets[i + 1]] for i in range(self.count)]
@@ -273,6 +289,22 @@ class Batch:
         _check(load().cme_transform(self.handle, int(sign), _dptr(out), HOST))
         return out.view(np.complex128)
 
+    def grad(self, h: float, nsteps: int, target, eps: float = 1e-20, segment: int = 0) -> dict:
+        """cme_grad: loss and gradients of the log-power-spectrum misfit after nsteps RK4IP
+        steps from the current field (the batch ends at the final field)."""
+        T = np.ascontiguousarray(target, dtype=np.float64).reshape(-1)
+        assert T.size == self.total
+        C, M = self.count, self.total
+        out = {"loss": np.zeros(C), "d_sigma": np.zeros(C), "d_A_in": np.zeros(2 * C),
+               "d_D2": np.zeros(C), "d_D3": np.zeros(C), "d_omega": np.zeros(M),
+               "d_kappa": np.zeros(M), "d_D0": np.zeros(2 * M)}
+        g = Grads(**{k: _dptr(v) for k, v in out.items()})
+        _check(load().cme_grad(self.handle, float(h), int(nsteps), _dptr(T), float(eps),
+                               int(segment), ctypes.byref(g)))
+        out["d_A_in"] = out["d_A_in"].view(np.complex128)
+        out["d_D0"] = out["d_D0"].view(np.complex128)
+        return out
+
     def eval_rhs(self) -> np.ndarray:
         out = np.empty(2 * self.total, dtype=np.float64)
         _check(load().cme_eval_rhs(self.handle, _dptr(out), HOST))
@@ -287,3 +319,55 @@ def fma_peak(precision=FP32) -> float:
 
 def kernel_launches() -> int:
     return int(load().cme_kernel_launches())
+
+
+# ---- autograd ----------------------------------------------------------------------------------
+def _autograd_function():
+    import torch
+
+    class LogSpectrumLoss(torch.autograd.Function):
+        """Sum over a batch of the log-power-spectrum misfit after nsteps RK4IP steps, as a
+        differentiable function of (sigma, Re A_in, Im A_in, D2, D3, Re D0, Im D0) per
+        instance.  The forward pass and the discrete adjoint both run in the CUDA library
+        (cme_grad); this class only marshals tensors (float64, CPU) to and from it."""
+
+        @staticmethod
+        def forward(ctx, sigma, a_re, a_im, D2, D3, d0_re, d0_im, spec):
+            B, N = d0_re.shape
+            mu = np.arange(N) - N // 2
+            insts = []
+            for b in range(B):
+                om = float(D2[b]) * mu * mu / 2.0 + float(D3[b]) * mu ** 3 / 6.0
+                D0 = d0_re[b].detach().numpy() + 1j * d0_im[b].detach().numpy()
+                insts.append(Instance(N, np.full(N, spec["kappa"]), om, spec["g0"],
+                                      spec["kappa_ext"], complex(float(a_re[b]), float(a_im[b])),
+                                      float(sigma[b]), D0))
+            batch = Batch(insts, precision=spec.get("precision", FP64))
+            g = batch.grad(spec["h"], spec["nsteps"], spec["target"], spec.get("eps", 1e-20),
+                           spec.get("segment", 0))
+            batch.close()
+            t = lambda a: torch.as_tensor(np.asarray(a), dtype=torch.float64)
+            dD0 = g["d_D0"].reshape(B, N)
+            ctx.save_for_backward(t(g["d_sigma"]), t(g["d_A_in"].real), t(g["d_A_in"].imag),
+                                  t(g["d_D2"]), t(g["d_D3"]), t(dD0.real), t(dD0.imag))
+            return t(g["loss"]).sum()
+
+        @staticmethod
+        def backward(ctx, go):
+            return tuple(go * x for x in ctx.saved_tensors) + (None,)
+
+    return LogSpectrumLoss
+
+
+_LSL = None
+
+
+def log_spectrum_loss(sigma, a_re, a_im, D2, D3, d0_re, d0_im, *, kappa, kappa_ext, g0, h,
+                      nsteps, target, precision=FP64, eps=1e-20, segment=0):
+    """Differentiable (torch.autograd) batch loss; see LogSpectrumLoss."""
+    global _LSL
+    if _LSL is None:
+        _LSL = _autograd_function()
+    spec = dict(kappa=kappa, kappa_ext=kappa_ext, g0=g0, h=h, nsteps=nsteps, target=target,
+                precision=precision, eps=eps, segment=segment)
+    return _LSL.apply(sigma, a_re, a_im, D2, D3, d0_re, d0_im, spec)

@@ -182,6 +182,96 @@ __global__ void fma_kernel(T* out, int iters, T a, T b)
         out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void loss_seed_kernel(int prec, int total, const int* mode_inst, const int* inst_N,
+                                 const long long* inst_off, const void* hi, const void* lo,
+                                 const double* target, double eps, double* loss, void* dbar)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= total)
+        return;
+    const int i = mode_inst[m];
+    const int N = inst_N[i];
+    const long long off = inst_off[i];
+    double2 v;
+    if (prec == PREC_FP64) {
+        v = reinterpret_cast<const double2*>(hi)[m];
+    } else {
+        const float2 a = reinterpret_cast<const float2*>(hi)[m];
+        const float2 b = reinterpret_cast<const float2*>(lo)[m];
+        v = make_double2((double)a.x + (double)b.x, (double)a.y + (double)b.y);
+    }
+    const double P = v.x * v.x + v.y * v.y;
+    const double r = log10(P + eps) - target[off + centred_of((int)(m - off), N)];
+    loss[m] = r * r;   // per mode; summed per instance in a fixed order by grad_reduce
+    const double g = 4.0 * r / ((P + eps) * 2.302585092994045684);  // 2 dL/dP, d|D|^2 = 2 Re(conj D dD)
+    if (prec == PREC_FP64)
+        reinterpret_cast<double2*>(dbar)[m] = make_double2(g * v.x, g * v.y);
+    else
+        reinterpret_cast<float2*>(dbar)[m] = make_float2((float)(g * v.x), (float)(g * v.y));
+}
+
+__global__ void grad_reduce_kernel(const int* inst_N, const long long* inst_off, const double2* gL,
+                                   const double* loss_modes, double* red)
+{
+    const int i = blockIdx.x;
+    const int N = inst_N[i];
+    const long long off = inst_off[i];
+    double s0 = 0, s2 = 0, s3 = 0, sl = 0;
+    for (int pm = threadIdx.x; pm < N; pm += blockDim.x) {
+        const double mu = pm < N / 2 ? pm : pm - N;   // transform position -> mode number
+        const double g = gL[off + pm].y;
+        s0 += g;
+        s2 += g * mu * mu * 0.5;
+        s3 += g * mu * mu * mu / 6.0;
+        sl += loss_modes[off + pm];
+    }
+    __shared__ double sh[4][256];
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s2;
+    sh[2][threadIdx.x] = s3;
+    sh[3][threadIdx.x] = sl;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 4; ++k)
+                sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        red[4 * i + 0] = sh[0][0];
+        red[4 * i + 1] = sh[1][0];
+        red[4 * i + 2] = sh[2][0];
+        red[4 * i + 3] = sh[3][0];
+    }
+}
+
+__global__ void grad_export_kernel(int prec, int total, const int* mode_inst, const int* inst_N,
+                                   const long long* inst_off, const void* dbar,
+                                   const double2* gL, const double* red, double2* dD0,
+                                   double* domega, double* dkappa)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= total)
+        return;
+    const int i = mode_inst[m];
+    const int N = inst_N[i];
+    const long long off = inst_off[i];
+    const long long c = off + centred_of((int)(m - off), N);
+    double2 d;
+    if (prec == PREC_FP64) {
+        d = reinterpret_cast<const double2*>(dbar)[m];
+    } else {
+        const float2 a = reinterpret_cast<const float2*>(dbar)[m];
+        d = make_double2(a.x, a.y);
+    }
+    if (dD0)
+        dD0[c] = d;
+    if (domega)
+        domega[c] = gL[m].y - (m == off ? red[4 * i] : 0.0);
+    if (dkappa)
+        dkappa[c] = -0.5 * gL[m].x;
+}
+
 inline int nblocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -227,6 +317,35 @@ cudaError_t launch_export_plain(int prec, int total, const int* mode_inst, const
     export_plain_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N,
                                                              inst_off, src, dst,
                                                              reorder_centred);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_seed(int prec, int total, const int* mode_inst, const int* inst_N,
+                             const long long* inst_off, const void* hi, const void* lo,
+                             const double* target, double eps, double* loss, void* dbar,
+                             cudaStream_t s)
+{
+    loss_seed_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N, inst_off,
+                                                          hi, lo, target, eps, loss, dbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_reduce(int count, const int* inst_N, const long long* inst_off,
+                               const double2* gL, const double* loss_modes, double* red,
+                               cudaStream_t s)
+{
+    grad_reduce_kernel<<<count, 256, 0, s>>>(inst_N, inst_off, gL, loss_modes, red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_export(int prec, int total, const int* mode_inst, const int* inst_N,
+                               const long long* inst_off, const void* dbar, const double2* gL,
+                               const double* red, double2* dD0, double* domega, double* dkappa,
+                               cudaStream_t s)
+{
+    grad_export_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N,
+                                                            inst_off, dbar, gL, red, dD0, domega,
+                                                            dkappa);
     return cudaGetLastError();
 }
 

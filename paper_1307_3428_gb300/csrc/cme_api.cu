@@ -16,6 +16,7 @@
 
 #include "cme.h"
 #include "cme_internal.h"
+#include "cme_adjoint_args.h"
 
 using namespace cme;
 
@@ -93,7 +94,7 @@ bool shape_compiled(int logN, int R)
     static const int shapes[][2] = {{2, 4},  {3, 8},  {4, 8},  {4, 16}, {5, 8},  {5, 16},
                                     {6, 8},  {6, 4},  {6, 16}, {7, 8},  {7, 4},  {7, 16},
                                     {8, 8},  {8, 4},  {8, 16}, {9, 8},  {9, 4},  {10, 8},
-                                    {10, 4}, {11, 8}, {12, 8}};
+                                    {10, 4}, {11, 8}, {11, 16}, {12, 8}, {12, 16}};
     for (auto& s : shapes)
         if (s[0] == logN && s[1] == R)
             return true;
@@ -151,6 +152,33 @@ struct cme_batch_s {
 
     std::map<std::pair<double, long>, std::pair<cudaGraphExec_t, int>> graphs;
 
+    // launch plan: 1 = one kernel per group (concurrent side streams when there are several
+    // groups), 2 = one persistent work-list kernel over all groups
+    int mode = 1;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;      // ev[0] fork, ev[1 + i] join of side stream i
+    FusedTile* tiles_d = nullptr;
+    std::vector<double> sqk_h;        // sqrt(kappa_ext) per instance
+
+    // gradient scratch (allocated by the first cme_grad call, grown when needed)
+    long long g_S = 0, g_K = 0;
+    void *g_ckpt_hi = nullptr, *g_ckpt_lo = nullptr, *g_seg = nullptr, *g_ybuf = nullptr,
+         *g_dbar = nullptr;
+    double2 *g_gL = nullptr, *g_pbar = nullptr, *g_dD0 = nullptr;
+    double *g_loss = nullptr, *g_red = nullptr, *g_target = nullptr, *g_domega = nullptr,
+           *g_dkappa = nullptr;
+    std::vector<void*> g_allocs;
+    int* counter_d = nullptr;
+    int ntiles = 0;
+    int sms = 0;
+
+    void clear_graphs()
+    {
+        for (auto& kv : graphs)
+            cudaGraphExecDestroy(kv.second.first);
+        graphs.clear();
+    }
+
     void* alloc(size_t bytes)
     {
         void* p = dev_alloc(bytes);
@@ -159,6 +187,77 @@ struct cme_batch_s {
         return p;
     }
 };
+
+namespace {
+
+// (Re)compute the launch plan of every group from the options: values per thread R and
+// instances per block G of the per-group kernels, and the persistent work-list tiles.
+int plan_batch(cme_batch b, const cme_options& o)
+{
+    if (o.steps_per_launch < 0 || o.inst_per_cta < 0 || o.radix < 0 || o.persistent < 0 ||
+        o.persistent > 2)
+        return fail(CME_ERR_INVALID_ARG, "launch plan: invalid option");
+    for (auto& g : b->groups) {
+        int R = o.radix ? o.radix : default_radix(g.logN);
+        if (R > g.N)
+            R = g.N;
+        if (!shape_compiled(g.logN, R))
+            return fail(CME_ERR_INVALID_ARG, "launch plan: radix %d not available for N=%d", R, g.N);
+        g.R = R;
+        const int P = g.N / R;
+        int G = o.inst_per_cta;
+        if (G == 0)
+            G = P >= 64 ? 1 : std::max(1, 64 / P);
+        G = std::min(G, std::max(1, 256 / P));
+        if (P >= 64) {
+            G = 1;  // kernels for groups of >= 64 threads are compiled for one instance per block
+        } else if (P < 32) {
+            // groups narrower than a warp synchronise with __syncwarp over full warps: make the
+            // block a whole number of warps (surplus groups recompute the last instance and
+            // store nothing)
+            const int per_warp = 32 / P;
+            G = std::max(per_warp, (G + per_warp - 1) / per_warp * per_warp);
+        } else {
+            G = std::min(G, g.count);
+        }
+        g.G = G;
+    }
+    int mode = o.persistent;
+    if (mode == 0)
+        mode = b->groups.size() > 1 ? 2 : 1;
+    if (mode == 2) {
+        // tiles of 256 / P instances (the fused kernel's own values per thread), heaviest first;
+        // a tile's time scales with R log2 N
+        std::vector<std::pair<int, FusedTile>> tiles;
+        for (int gi = 0; gi < (int)b->groups.size(); ++gi) {
+            const auto& g = b->groups[gi];
+            const int Rf = fused_radix(g.logN), Pf = g.N / Rf;
+            const int Gf = std::max(1, FUSED_THREADS / Pf);
+            for (int f = 0; f < g.count; f += Gf)
+                tiles.push_back({Rf * g.logN, FusedTile{gi, f}});
+        }
+        std::stable_sort(tiles.begin(), tiles.end(),
+                         [](const auto& x, const auto& y) { return x.first > y.first; });
+        std::vector<FusedTile> t(tiles.size());
+        for (size_t i = 0; i < tiles.size(); ++i)
+            t[i] = tiles[i].second;
+        b->ntiles = (int)t.size();
+        CME_CUDA(cudaMemcpyAsync(b->tiles_d, t.data(), t.size() * sizeof(FusedTile),
+                                 cudaMemcpyHostToDevice, b->stream),
+                 "launch plan: tiles");
+        CME_CUDA(cudaStreamSynchronize(b->stream), "launch plan: tiles");
+    }
+    b->mode = mode;
+    b->opt.radix = o.radix;
+    b->opt.inst_per_cta = o.inst_per_cta;
+    b->opt.steps_per_launch = o.steps_per_launch;
+    b->opt.use_graph = o.use_graph;
+    b->opt.persistent = mode;
+    b->clear_graphs();
+    return CME_OK;
+}
+
+}  // namespace
 
 // ------------------------------------------------------------------------------------------
 extern "C" {
@@ -237,8 +336,13 @@ void cme_batch_destroy(cme_batch b)
         return;
     if (b->stream)
         cudaStreamSynchronize(b->stream);
-    for (auto& kv : b->graphs)
-        cudaGraphExecDestroy(kv.second.first);
+    b->clear_graphs();
+    for (void* p : b->g_allocs)
+        dev_free(p, b->free_fn, b->free_ctx);
+    for (cudaStream_t st : b->side)
+        cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->ev)
+        cudaEventDestroy(e);
     for (void* p : b->allocs)
         dev_free(p, b->free_fn, b->free_ctx);
     if (b->own_stream && b->stream)
@@ -313,35 +417,24 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         g.first = i;
         g.count = j - i;
         g.base = b->off_h[i];
-        int R = o.radix ? o.radix : default_radix(g.logN);
-        if (R > g.N)
-            R = g.N;
-        if (!shape_compiled(g.logN, R)) {
-            cme_batch_destroy(b);
-            return fail(CME_ERR_INVALID_ARG, "cme_batch_create: radix %d not available for N=%d", R, g.N);
-        }
-        g.R = R;
-        const int P = g.N / R;
-        int G = o.inst_per_cta;
-        if (G == 0)
-            G = P >= 64 ? 1 : std::max(1, 64 / P);
-        G = std::min(G, std::max(1, 256 / P));
-        if (P >= 64) {
-            G = 1;  // kernels for groups of >= 64 threads are compiled for one instance per block
-        } else if (P < 32) {
-            // groups narrower than a warp synchronise with __syncwarp over full warps: make the
-            // block a whole number of warps (surplus groups recompute the last instance and
-            // store nothing)
-            const int per_warp = 32 / P;
-            G = std::max(per_warp, (G + per_warp - 1) / per_warp * per_warp);
-        } else {
-            G = std::min(G, g.count);
-        }
-        g.G = G;
         b->groups.push_back(g);
         i = j;
     }
 
+    if (b->groups.size() > (size_t)MAX_GROUPS) {
+        cme_batch_destroy(b);
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_create: more than %d distinct N", MAX_GROUPS);
+    }
+    // host-side validation of the launch options before any CUDA call
+    for (auto& g : b->groups) {
+        const int R = std::min(o.radix ? o.radix : default_radix(g.logN), g.N);
+        if (!shape_compiled(g.logN, R) || o.persistent < 0 || o.persistent > 2) {
+            cme_batch_destroy(b);
+            return fail(CME_ERR_INVALID_ARG,
+                        "cme_batch_create: launch option (radix %d, persistent %d) not available "
+                        "for N=%d", R, o.persistent, g.N);
+        }
+    }
     if (cuda_stream) {
         b->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -382,6 +475,8 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         if (!b->tw.count(g.logN))
             b->tw[g.logN] = A((size_t)g.N * b->elem);
     }
+    b->tiles_d = (FusedTile*)A(count * sizeof(FusedTile));
+    b->counter_d = (int*)A(64);
     if (!ok) {
         cme_batch_destroy(b);
         return fail(CME_ERR_OOM, "cme_batch_create: device allocation of %lld modes failed",
@@ -405,6 +500,7 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         }
         g0[i] = v[i]->g0;
         const double sk = std::sqrt(v[i]->kappa_ext);
+        b->sqk_h.push_back(sk);
         pump[i] = make_double2(sk * v[i]->ain_re, sk * v[i]->ain_im);
     }
     cudaStream_t s = b->stream;
@@ -445,6 +541,33 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     if (e != cudaSuccess) {
         cme_batch_destroy(b);
         return cuda_fail(e, "cme_batch_create: set-up kernels");
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (b->groups.size() > 1) {
+        b->side.resize(b->groups.size());
+        b->ev.resize(b->groups.size() + 1);
+        for (auto& st : b->side) {
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e != cudaSuccess)
+                break;
+        }
+        for (auto& ev : b->ev) {
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            cme_batch_destroy(b);
+            return cuda_fail(e, "cme_batch_create: side streams");
+        }
+    }
+    const int rc = plan_batch(b, o);
+    if (rc) {
+        const std::string msg = g_err;
+        cme_batch_destroy(b);
+        g_err = msg;
+        return rc;
     }
     *out = b;
     return CME_OK;
@@ -494,16 +617,57 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
     return a;
 }
 
-cudaError_t launch_group_step(cme_batch b, const LaunchGroup& g, long long nsteps)
+cudaError_t launch_group_step(cme_batch b, const LaunchGroup& g, long long nsteps,
+                              cudaStream_t st)
 {
     StepArgs a = group_args(b, g);
     a.nsteps = nsteps;
     ++g_launches;
     if (b->prec == PREC_FP64)
-        return b->method == METHOD_RK4IP ? launch_step_fp64_rk4ip(g.logN, g.R, a, b->stream)
-                                         : launch_step_fp64_strang(g.logN, g.R, a, b->stream);
-    return b->method == METHOD_RK4IP ? launch_step_fp32_rk4ip(g.logN, g.R, a, b->stream)
-                                     : launch_step_fp32_strang(g.logN, g.R, a, b->stream);
+        return b->method == METHOD_RK4IP ? launch_step_fp64_rk4ip(g.logN, g.R, a, st)
+                                         : launch_step_fp64_strang(g.logN, g.R, a, st);
+    return b->method == METHOD_RK4IP ? launch_step_fp32_rk4ip(g.logN, g.R, a, st)
+                                     : launch_step_fp32_strang(g.logN, g.R, a, st);
+}
+
+// Dynamic shared memory of the work-list kernel: the largest tile, with every group's layout
+// (exchange buffers and, where used, the shared-memory accumulators) from group_smem_bytes.
+size_t fused_smem(cme_batch b)
+{
+    size_t m = 0;
+    const int tb = b->prec == PREC_FP32 ? 4 : 8;
+    for (auto& g : b->groups) {
+        const int Rf = fused_radix(g.logN);
+        const int Pf = g.N / Rf;
+        const size_t Gf = std::max(1, FUSED_THREADS / Pf);
+        m = std::max(m, Gf * group_smem_bytes(tb, g.logN, Rf));
+    }
+    return m;
+}
+
+cudaError_t launch_fused(cme_batch b, long long nsteps)
+{
+    FusedArgs fa{};
+    fa.ntiles = b->ntiles;
+    fa.tiles = b->tiles_d;
+    fa.counter = b->counter_d;
+    fa.ngroups = (int)b->groups.size();
+    for (int i = 0; i < fa.ngroups; ++i) {
+        const auto& g = b->groups[i];
+        fa.logN[i] = g.logN;
+        fa.g[i] = group_args(b, g);
+        fa.g[i].nsteps = nsteps;
+    }
+    const size_t smem = fused_smem(b);
+    if (smem > (size_t)227 * 1024)
+        return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaMemsetAsync(b->counter_d, 0, sizeof(int), b->stream);
+    if (e != cudaSuccess)
+        return e;
+    const int grid = std::max(1, std::min(b->ntiles, 2 * b->sms));
+    ++g_launches;
+    return b->prec == PREC_FP64 ? launch_fused_fp64(b->method, fa, grid, smem, b->stream)
+                                : launch_fused_fp32(b->method, fa, grid, smem, b->stream);
 }
 
 // Enqueue the step kernels for nsteps (chunked by steps_per_launch); returns kernels launched.
@@ -513,12 +677,29 @@ cudaError_t enqueue_steps(cme_batch b, long nsteps, int* nk)
     int k = 0;
     for (long done = 0; done < nsteps; done += chunk) {
         const long n = std::min(chunk, nsteps - done);
-        for (auto& g : b->groups) {
-            cudaError_t e = launch_group_step(b, g, n);
-            if (e != cudaSuccess)
-                return e;
+        cudaError_t e = cudaSuccess;
+        if (b->mode == 2) {
+            e = launch_fused(b, n);
             ++k;
+        } else if (b->groups.size() == 1) {
+            e = launch_group_step(b, b->groups[0], n, b->stream);
+            ++k;
+        } else {
+            // fork the groups onto side streams so that they run concurrently, then join
+            e = cudaEventRecord(b->ev[0], b->stream);
+            for (size_t i = 0; e == cudaSuccess && i < b->groups.size(); ++i) {
+                e = cudaStreamWaitEvent(b->side[i], b->ev[0], 0);
+                if (e == cudaSuccess)
+                    e = launch_group_step(b, b->groups[i], n, b->side[i]);
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(b->ev[1 + i], b->side[i]);
+                if (e == cudaSuccess)
+                    e = cudaStreamWaitEvent(b->stream, b->ev[1 + i], 0);
+                ++k;
+            }
         }
+        if (e != cudaSuccess)
+            return e;
     }
     if (nk)
         *nk = k;
@@ -595,6 +776,207 @@ int cme_step(cme_batch b, double h, long nsteps)
         CME_CUDA(enqueue_steps(b, nsteps, nullptr), "cme_step: kernel launch");
     }
     b->tau += h * (double)nsteps;
+    return CME_OK;
+}
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, cme_options> g_tune_cache;
+bool g_tune_loaded = false;
+
+// Key of a tuning result: device, precision, integrator, h and the multiset of N.
+std::string tune_key(cme_batch b, double h)
+{
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string k = prop.name;
+    char buf[96];
+    snprintf(buf, sizeof buf, "|p%d|m%d|h%.17g", b->prec, b->method, h);
+    k += buf;
+    for (auto& g : b->groups) {
+        snprintf(buf, sizeof buf, "|%dx%d", g.N, g.count);
+        k += buf;
+    }
+    return k;
+}
+
+// Optional persistence: CME_TUNE_CACHE names a text file of "key<TAB>radix G persistent" lines.
+void tune_cache_load()
+{
+    if (g_tune_loaded)
+        return;
+    g_tune_loaded = true;
+    const char* path = getenv("CME_TUNE_CACHE");
+    if (!path)
+        return;
+    FILE* f = fopen(path, "r");
+    if (!f)
+        return;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        char* tab = strchr(line, '\t');
+        if (!tab)
+            continue;
+        *tab = 0;
+        cme_options o;
+        cme_default_options(&o);
+        if (sscanf(tab + 1, "%d %d %d", &o.radix, &o.inst_per_cta, &o.persistent) == 3)
+            g_tune_cache[line] = o;
+    }
+    fclose(f);
+}
+
+void tune_cache_store(const std::string& key, const cme_options& o)
+{
+    g_tune_cache[key] = o;
+    const char* path = getenv("CME_TUNE_CACHE");
+    if (!path)
+        return;
+    FILE* f = fopen(path, "a");
+    if (!f)
+        return;
+    fprintf(f, "%s\t%d %d %d\n", key.c_str(), o.radix, o.inst_per_cta, o.persistent);
+    fclose(f);
+}
+
+}  // namespace
+
+int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out)
+{
+    if (!b || !(h > 0.0) || !std::isfinite(h) || probe_steps <= 0)
+        return fail(CME_ERR_INVALID_ARG, "cme_autotune: invalid argument");
+    const std::string key = tune_key(b, h);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            cme_options o = b->opt;
+            o.radix = it->second.radix;
+            o.inst_per_cta = it->second.inst_per_cta;
+            o.persistent = it->second.persistent;
+            int rc = plan_batch(b, o);
+            if (rc == CME_OK) {
+                if (plan_out)
+                    *plan_out = b->opt;
+                return CME_OK;
+            }
+        }
+    }
+    // candidates
+    std::vector<cme_options> cand;
+    cme_options base = b->opt;
+    base.steps_per_launch = 0;
+    if (b->groups.size() == 1) {
+        const auto& g = b->groups[0];
+        for (int R : {4, 8, 16}) {
+            if (R > g.N || !shape_compiled(g.logN, R))
+                continue;
+            for (int G : {0, 2, 4}) {
+                const int P = g.N / R;
+                if (G && (P >= 64 || G * P > 256))
+                    continue;
+                cme_options o = base;
+                o.radix = R;
+                o.inst_per_cta = G;
+                o.persistent = 1;
+                cand.push_back(o);
+            }
+        }
+        cme_options o = base;   // the work-list kernel also runs single-N batches
+        o.radix = 0;
+        o.inst_per_cta = 0;
+        o.persistent = 2;
+        cand.push_back(o);
+    } else {
+        for (int pers : {2, 1}) {
+            cme_options o = base;
+            o.radix = 0;
+            o.inst_per_cta = 0;
+            o.persistent = pers;
+            cand.push_back(o);
+        }
+    }
+    // save the field, time each candidate from the same state, restore
+    const size_t fb = (size_t)b->total * b->elem;
+    void* save = dev_alloc(fb * (b->prec == PREC_FP32 ? 2 : 1));
+    if (!save)
+        return fail(CME_ERR_OOM, "cme_autotune: no memory for the saved field");
+    cme_free_fn ffn;
+    void* fctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        ffn = g_free;
+        fctx = g_alloc_ctx;
+    }
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(b->hi, save, fb, cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess && b->prec == PREC_FP32)
+            e = cudaMemcpyAsync(b->lo, (char*)save + fb, fb, cudaMemcpyDeviceToDevice, b->stream);
+        return e;
+    };
+    cudaError_t e = cudaMemcpyAsync(save, b->hi, fb, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess && b->prec == PREC_FP32)
+        e = cudaMemcpyAsync((char*)save + fb, b->lo, fb, cudaMemcpyDeviceToDevice, b->stream);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t1);
+    int rc = CME_OK;
+    if (e == cudaSuccess)
+        rc = ensure_propagators(b, h);
+    float best = 1e30f;
+    cme_options best_o = b->opt;
+    for (size_t c = 0; e == cudaSuccess && rc == CME_OK && c < cand.size(); ++c) {
+        if (plan_batch(b, cand[c]) != CME_OK)
+            continue;
+        e = restore();
+        if (e == cudaSuccess)
+            e = enqueue_steps(b, std::max(1L, probe_steps / 4), nullptr);   // warm-up
+        if (e == cudaSuccess)
+            e = restore();
+        if (e == cudaSuccess)
+            e = cudaEventRecord(t0, b->stream);
+        if (e == cudaSuccess)
+            e = enqueue_steps(b, probe_steps, nullptr);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(t1, b->stream);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(t1);
+        float ms = 0;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            best_o = b->opt;
+        }
+    }
+    if (e == cudaSuccess)
+        e = restore();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    if (t0)
+        cudaEventDestroy(t0);
+    if (t1)
+        cudaEventDestroy(t1);
+    dev_free(save, ffn, fctx);
+    if (rc != CME_OK)
+        return rc;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cme_autotune");
+    rc = plan_batch(b, best_o);
+    if (rc != CME_OK)
+        return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_store(key, b->opt);
+    }
+    if (plan_out)
+        *plan_out = b->opt;
     return CME_OK;
 }
 
@@ -795,3 +1177,148 @@ int cme_fma_peak(int precision, double* flops_per_s)
 }
 
 }  // extern "C"
+
+namespace {
+
+int ensure_grad_scratch(cme_batch b, long long S, long long K)
+{
+    if (b->g_S >= S && b->g_K >= K && !b->g_allocs.empty())
+        return CME_OK;
+    for (void* p : b->g_allocs)
+        dev_free(p, b->free_fn, b->free_ctx);
+    b->g_allocs.clear();
+    const size_t T = (size_t)b->total, E = b->elem, C = (size_t)b->count;
+    bool ok = true;
+    auto A = [&](size_t bytes) {
+        void* p = dev_alloc(bytes);
+        if (p)
+            b->g_allocs.push_back(p);
+        else
+            ok = false;
+        return p;
+    };
+    b->g_ckpt_hi = A(S * T * E);
+    b->g_ckpt_lo = b->prec == PREC_FP32 ? A(S * T * E) : nullptr;
+    b->g_seg = A(K * T * E);
+    b->g_ybuf = A(3 * T * E);
+    b->g_dbar = A(T * E);
+    b->g_gL = (double2*)A(T * 16);
+    b->g_pbar = (double2*)A(C * 16);
+    b->g_dD0 = (double2*)A(T * 16);
+    b->g_loss = (double*)A(T * 8);   // per-mode loss terms
+    b->g_red = (double*)A(C * 32);
+    b->g_target = (double*)A(T * 8);
+    b->g_domega = (double*)A(T * 8);
+    b->g_dkappa = (double*)A(T * 8);
+    if (!ok) {
+        for (void* p : b->g_allocs)
+            dev_free(p, b->free_fn, b->free_ctx);
+        b->g_allocs.clear();
+        b->g_S = b->g_K = 0;
+        return fail(CME_ERR_OOM, "cme_grad: cannot allocate %lld checkpoints x %lld modes", S,
+                    (long long)T);
+    }
+    b->g_S = S;
+    b->g_K = K;
+    return CME_OK;
+}
+
+}  // namespace
+
+extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target, double eps,
+                        long segment, cme_grads* out)
+{
+    if (!b || !target || !out || !(h > 0.0) || !std::isfinite(h) || nsteps <= 0 || segment < 0 ||
+        !(eps > 0.0))
+        return fail(CME_ERR_INVALID_ARG, "cme_grad: invalid argument");
+    if (b->method != METHOD_RK4IP)
+        return fail(CME_ERR_INVALID_ARG, "cme_grad: gradients are implemented for RK4IP batches");
+    const long long K = segment ? segment : (long long)std::ceil(std::sqrt((double)nsteps));
+    const long long S = (nsteps + K - 1) / K;
+    int rc = ensure_grad_scratch(b, S, K);
+    if (rc)
+        return rc;
+    rc = ensure_propagators(b, h);
+    if (rc)
+        return rc;
+    const size_t fb = (size_t)b->total * b->elem;
+    cudaStream_t st = b->stream;
+    // forward with checkpoints at the segment starts
+    for (long long s = 0; s < S; ++s) {
+        CME_CUDA(cudaMemcpyAsync((char*)b->g_ckpt_hi + s * fb, b->hi, fb, cudaMemcpyDeviceToDevice, st),
+                 "cme_grad: checkpoint");
+        if (b->prec == PREC_FP32)
+            CME_CUDA(cudaMemcpyAsync((char*)b->g_ckpt_lo + s * fb, b->lo, fb,
+                                     cudaMemcpyDeviceToDevice, st),
+                     "cme_grad: checkpoint");
+        const long long n = std::min(K, (long long)nsteps - s * K);
+        CME_CUDA(enqueue_steps(b, (long)n, nullptr), "cme_grad: forward");
+    }
+    // loss and its seed
+    CME_CUDA(cudaMemcpyAsync(b->g_target, target, (size_t)b->total * 8, cudaMemcpyHostToDevice, st),
+             "cme_grad: target");
+    ++g_launches;
+    CME_CUDA(launch_loss_seed(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, b->hi,
+                              b->lo, b->g_target, eps, b->g_loss, b->g_dbar, st),
+             "cme_grad: seed");
+    // backward, one launch per group
+    for (auto& g : b->groups) {
+        AdjArgs A{};
+        A.s = group_args(b, g);
+        A.nsteps = nsteps;
+        A.K = K;
+        A.S = S;
+        A.total = b->total;
+        A.ckpt_hi = b->g_ckpt_hi;
+        A.ckpt_lo = b->g_ckpt_lo ? b->g_ckpt_lo : b->g_ckpt_hi;
+        A.seg = b->g_seg;
+        A.ybuf = b->g_ybuf;
+        A.dbar = b->g_dbar;
+        A.gL = b->g_gL;
+        A.pbar = b->g_pbar + g.first;
+        ++g_launches;
+        cudaError_t e = b->prec == PREC_FP64 ? launch_adjoint_fp64(g.logN, g.R, A, st)
+                                             : launch_adjoint_fp32(g.logN, g.R, A, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cme_grad: adjoint kernel");
+    }
+    g_launches += 2;
+    CME_CUDA(launch_grad_reduce(b->count, b->inst_N, b->inst_off, b->g_gL, b->g_loss, b->g_red, st),
+             "cme_grad: reduce");
+    CME_CUDA(launch_grad_export(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off,
+                                b->g_dbar, b->g_gL, b->g_red, b->g_dD0, b->g_domega, b->g_dkappa, st),
+             "cme_grad: export");
+    std::vector<double> red(4 * (size_t)b->count), pb(2 * (size_t)b->count);
+    CME_CUDA(cudaMemcpyAsync(red.data(), b->g_red, red.size() * 8, cudaMemcpyDeviceToHost, st),
+             "cme_grad: copy");
+    CME_CUDA(cudaMemcpyAsync(pb.data(), b->g_pbar, pb.size() * 8, cudaMemcpyDeviceToHost, st),
+             "cme_grad: copy");
+    if (out->d_D0)
+        CME_CUDA(cudaMemcpyAsync(out->d_D0, b->g_dD0, (size_t)b->total * 16, cudaMemcpyDeviceToHost, st),
+                 "cme_grad: copy");
+    if (out->d_omega)
+        CME_CUDA(cudaMemcpyAsync(out->d_omega, b->g_domega, (size_t)b->total * 8,
+                                 cudaMemcpyDeviceToHost, st),
+                 "cme_grad: copy");
+    if (out->d_kappa)
+        CME_CUDA(cudaMemcpyAsync(out->d_kappa, b->g_dkappa, (size_t)b->total * 8,
+                                 cudaMemcpyDeviceToHost, st),
+                 "cme_grad: copy");
+    CME_CUDA(cudaStreamSynchronize(st), "cme_grad: sync");
+    for (int i = 0; i < b->count; ++i) {
+        if (out->loss)
+            out->loss[i] = red[4 * i + 3];
+        if (out->d_sigma)
+            out->d_sigma[i] = -red[4 * i];
+        if (out->d_D2)
+            out->d_D2[i] = red[4 * i + 1];
+        if (out->d_D3)
+            out->d_D3[i] = red[4 * i + 2];
+        if (out->d_A_in) {
+            out->d_A_in[2 * i] = b->sqk_h[i] * pb[2 * i];
+            out->d_A_in[2 * i + 1] = b->sqk_h[i] * pb[2 * i + 1];
+        }
+    }
+    b->tau += h * (double)nsteps;
+    return CME_OK;
+}

@@ -247,8 +247,8 @@ struct Transform {
     using PL = Plan<LOGN, R>;
     static constexpr int N = PL::N, P = PL::P, NS = PL::NS;
 
-    template <int s, int S>
-    CME_DEV static void pass(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1])
+    template <int s, int S, class TW>
+    CME_DEV static void pass(cx<T> (&x)[R], const TW& tw)
     {
         constexpr int r = PL::radix(s), Q = R / r;
 #pragma unroll
@@ -260,7 +260,7 @@ struct Transform {
             if constexpr (s > 0) {
 #pragma unroll
                 for (int j = 1; j < r; ++j) {
-                    const cx<T> w = tw[(s - 1) * (R - 1) + q * (r - 1) + (j - 1)];
+                    const cx<T> w = tw.template get<s>(q, j);
                     v[j] = (S > 0) ? cmul(v[j], w) : cmulc(v[j], w);
                 }
             }
@@ -310,47 +310,90 @@ struct Transform {
 
     // buf: the first of two ping-pong buffers (the second starts BUF elements later); par
     // selects the one the next exchange writes.
-    template <int s, int S>
-    CME_DEV static void run_from(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1],
-                                 const Xbuf<T>& buf, int& par, const Addr& ad)
+    template <int s, int S, class TW>
+    CME_DEV static void run_from(cx<T> (&x)[R], const TW& tw, const Xbuf<T>& buf, int& par,
+                                 const Addr& ad)
     {
         pass<s, S>(x, tw);
         if constexpr (s + 1 < NS) {
             exchange<s>(x, buf.at(par * PL::BUF), ad);
             par ^= 1;
-            run_from<s + 1, S>(x, tw, buf, par, ad);
+            run_from<s + 1, S, TW>(x, tw, buf, par, ad);
         }
     }
 
-    template <int S>
-    CME_DEV static void run(cx<T> (&x)[R], const cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1],
-                            const Xbuf<T>& buf, int& par, const Addr& ad)
+    template <int S, class TW>
+    CME_DEV static void run(cx<T> (&x)[R], const TW& tw, const Xbuf<T>& buf, int& par,
+                            const Addr& ad)
     {
-        run_from<0, S>(x, tw, buf, par, ad);
+        run_from<0, S, TW>(x, tw, buf, par, ad);
     }
 
-    // Twiddles exp(2 pi i j k / (L r)), k = (t + qP) mod L, from the table exp(2 pi i m/N).
+};
+
+// Twiddles exp(2 pi i j k / (L r)) of pass s >= 1 for butterfly q of thread t, where
+// k = (t + qP) mod L, taken from the table exp(2 pi i m / N).  IN_REGS = true loads all of
+// them into registers once per launch; otherwise each pass reads them from the table through
+// the read-only cache (large N, where registers are scarce).
+template <typename T, int LOGN, int R, bool IN_REGS>
+struct Twiddles;
+
+template <typename T, int LOGN, int R>
+struct Twiddles<T, LOGN, R, true> {
+    using PL = Plan<LOGN, R>;
+    cx<T> w[PL::NTW > 0 ? PL::NTW : 1];
+
     template <int s>
-    CME_DEV static void load_tw_from(cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1], const void* table, int t)
+    CME_DEV void init_from(const void* table, int t)
     {
-        if constexpr (s < NS) {
+        if constexpr (s < PL::NS) {
             constexpr int r = PL::radix(s), Q = R / r, L = PL::L(s);
-            constexpr int stride = N / (L * r);
+            constexpr int stride = PL::N / (L * r);
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const int k = (t + q * P) & (L - 1);
+                const int k = (t + q * PL::P) & (L - 1);
 #pragma unroll
                 for (int j = 1; j < r; ++j)
-                    tw[(s - 1) * (R - 1) + q * (r - 1) + (j - 1)] =
-                        gload<T>(table, (j * k * stride) & (N - 1));
+                    w[(s - 1) * (R - 1) + q * (r - 1) + (j - 1)] =
+                        gload<T>(table, (j * k * stride) & (PL::N - 1));
             }
-            load_tw_from<s + 1>(tw, table, t);
+            init_from<s + 1>(table, t);
         }
     }
-    CME_DEV static void load_tw(cx<T> (&tw)[PL::NTW > 0 ? PL::NTW : 1], const void* table, int t)
+    CME_DEV void init(const void* table, int t)
     {
-        if constexpr (NS > 1)
-            load_tw_from<1>(tw, table, t);
+        if constexpr (PL::NS > 1)
+            init_from<1>(table, t);
+    }
+    template <int s>
+    CME_DEV cx<T> get(int q, int j) const
+    {
+        constexpr int r = PL::radix(s);
+        return w[(s - 1) * (R - 1) + q * (r - 1) + (j - 1)];
+    }
+};
+
+template <typename T, int LOGN, int R>
+struct Twiddles<T, LOGN, R, false> {
+    using PL = Plan<LOGN, R>;
+    const cx<T>* table;
+    int kst[PL::NS > 1 ? PL::NS : 1];  // (t mod L_s) * N / (L_s r_s) per pass
+
+    CME_DEV void init(const void* tbl, int t)
+    {
+        table = reinterpret_cast<const cx<T>*>(tbl);
+#pragma unroll
+        for (int s = 1; s < PL::NS; ++s) {
+            const int L = PL::L(s), r = PL::radix(s);
+            kst[s] = (t & (L - 1)) * (PL::N / (L * r));
+        }
+    }
+    template <int s>
+    CME_DEV cx<T> get(int q, int j) const
+    {
+        // butterfly q > 0 only occurs in the last pass, where k = t + qP exactly
+        constexpr int r = PL::radix(s), L = PL::L(s), stride = PL::N / (L * r);
+        return gload<T>(table, (j * kst[s] + j * q * PL::P * stride) & (PL::N - 1));
     }
 };
 

@@ -33,6 +33,20 @@ struct StepArgs {
     void* diag_out;         // diagnostics output (same layout as the field)
 };
 
+// Shared-memory footprint of one instance group (one instance of N = 2^logN handled by N/R
+// threads): two padded ping-pong exchange buffers, plus -- for wide groups whose registers are
+// scarce -- the Runge-Kutta accumulator S and (FP32) the compensation word of the field.
+__host__ __device__ constexpr bool acc_in_smem(int tbytes, int logN, int R)
+{
+    return tbytes == 4 ? R >= 16 : logN >= 11;
+}
+__host__ __device__ constexpr size_t group_smem_bytes(int tbytes, int logN, int R)
+{
+    return (size_t)2 * (tbytes == 4 ? 1 : 2) * ((1 << logN) + (1 << logN) / 16 + 1) * 8 +
+           (acc_in_smem(tbytes, logN, R) ? (size_t)(1 << logN) * 2 * tbytes * (tbytes == 4 ? 2 : 1)
+                                         : 0);
+}
+
 // Launch one uniform-N group; implemented per precision and method in the kernel units.
 cudaError_t launch_step_fp64_rk4ip(int logN, int R, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp64_strang(int logN, int R, const StepArgs& a, cudaStream_t s);
@@ -74,5 +88,54 @@ cudaError_t launch_export_plain(int prec, int total, const int* mode_inst, const
                                 const long long* inst_off, const void* src, double2* dst,
                                 int reorder_centred, cudaStream_t s);
 cudaError_t run_fma_peak(int prec, double* flops);
+
+// Gradient helpers (aux_kernels.cu).
+// Log-power-spectrum misfit terms (log10(|D_mu|^2 + eps) - T_mu)^2 per mode (loss_modes) and
+// the cotangent dbar = dL/dRe D + i dL/dIm D in the field precision (transform order).
+cudaError_t launch_loss_seed(int prec, int total, const int* mode_inst, const int* inst_N,
+                             const long long* inst_off, const void* hi, const void* lo,
+                             const double* target, double eps, double* loss_modes, void* dbar,
+                             cudaStream_t s);
+// Per instance, in a fixed summation order: red[4i..4i+3] = (sum_mu g_mu, sum g_mu mu^2/2,
+// sum g_mu mu^3/6, L_i) with g_mu = Im gL_mu (the cotangent of Im L_mu = omega_mu - omega_0 -
+// sigma) and L_i the instance's loss.
+cudaError_t launch_grad_reduce(int count, const int* inst_N, const long long* inst_off,
+                               const double2* gL, const double* loss_modes, double* red,
+                               cudaStream_t s);
+// Centred FP64 outputs: dD0 (complex), domega = g - delta_{mu,0} sum g, dkappa = -Re gL / 2.
+cudaError_t launch_grad_export(int prec, int total, const int* mode_inst, const int* inst_N,
+                               const long long* inst_off, const void* dbar, const double2* gL,
+                               const double* red, double2* dD0, double* domega, double* dkappa,
+                               cudaStream_t s);
+struct AdjArgs;  // cme_adjoint_args.h
+cudaError_t launch_adjoint_fp32(int logN, int R, const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_fp64(int logN, int R, const AdjArgs& a, cudaStream_t s);
+
+}  // namespace cme
+
+namespace cme {
+
+// One persistent launch for a batch with several N: blocks of 256 threads take tiles
+// (group, first instance) from a work counter, heaviest first; each tile runs the uniform
+// step body of its N on 256/P instances.
+constexpr int FUSED_THREADS = 256;
+constexpr int MAX_GROUPS = 12;
+struct FusedTile {
+    int group;
+    int first;   // group-relative first instance
+};
+struct FusedArgs {
+    int ntiles;
+    const FusedTile* tiles;  // heaviest first
+    int* counter;            // zeroed before each launch
+    int ngroups;
+    int logN[MAX_GROUPS];
+    StepArgs g[MAX_GROUPS];  // per group; G is the tile width 256 / P
+};
+// Values per thread the fused kernel uses for N = 2^logN (P = N/R <= 256).
+inline int fused_radix(int logN) { return logN <= 2 ? 4 : (logN >= 12 ? 16 : 8); }
+size_t fused_smem_bytes(int prec, const int* logN, int ngroups);
+cudaError_t launch_fused_fp32(int method, const FusedArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_fused_fp64(int method, const FusedArgs& a, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace cme

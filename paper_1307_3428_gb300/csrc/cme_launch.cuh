@@ -17,16 +17,13 @@ namespace cme {
     X(8, 8) X(8, 4) X(8, 16)           \
     X(9, 8) X(9, 4)                    \
     X(10, 8) X(10, 4)                  \
-    X(11, 8)                           \
-    X(12, 8)
+    X(11, 8) X(11, 16)                 \
+    X(12, 8) X(12, 16)
 
 template <typename T>
-inline size_t smem_bytes_for(int logN, int G)
+inline size_t smem_bytes_for(int logN, int R, int G)
 {
-    const int N = 1 << logN;
-    const int BUF = N + N / 16 + 1;
-    const int W = sizeof(T) == 4 ? 1 : 2;
-    return (size_t)G * 2 * W * BUF * 8;
+    return (size_t)G * group_smem_bytes(sizeof(T), logN, R);
 }
 
 template <typename KernelT>
@@ -43,7 +40,7 @@ inline cudaError_t launch_step_shape(const StepArgs& a, cudaStream_t s)
     constexpr int P = Plan<LOGN, R>::P;
     const int threads = P * a.G;
     const int blocks = (a.ninst + a.G - 1) / a.G;
-    const size_t smem = smem_bytes_for<T>(LOGN, a.G);
+    const size_t smem = smem_bytes_for<T>(LOGN, R, a.G);
     auto k = step_kernel<T, LOGN, R, METHOD>;
     cudaError_t e = prepare_smem(k, smem);
     if (e != cudaSuccess)
@@ -58,7 +55,7 @@ inline cudaError_t launch_diag_shape(const StepArgs& a, cudaStream_t s)
     constexpr int P = Plan<LOGN, R>::P;
     const int threads = P * a.G;
     const int blocks = (a.ninst + a.G - 1) / a.G;
-    const size_t smem = smem_bytes_for<T>(LOGN, a.G);
+    const size_t smem = smem_bytes_for<T>(LOGN, R, a.G);
     auto k = diag_kernel<T, LOGN, R>;
     cudaError_t e = prepare_smem(k, smem);
     if (e != cudaSuccess)

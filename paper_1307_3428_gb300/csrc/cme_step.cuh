@@ -61,6 +61,10 @@ struct Props {
     }
 };
 
+// Twiddles stay in registers up to N = 1024 (FP32) / 512 (FP64).
+template <typename T, int LOGN>
+constexpr bool twiddles_in_regs() { return sizeof(T) == 4 ? LOGN <= 10 : LOGN <= 9; }
+
 // Per-thread view of one instance: the transform machinery plus the instance constants.
 template <typename T, int LOGN, int R>
 struct Group {
@@ -69,12 +73,13 @@ struct Group {
     static constexpr bool WARP = (P <= 32);
     static constexpr bool COMP = (sizeof(T) == 4);  // compensated state in FP32
     using TF = Transform<T, LOGN, R, WARP>;
+    using TW = Twiddles<T, LOGN, R, twiddles_in_regs<T, LOGN>()>;
 
     int t;
     int par;
     Xbuf<T> buf;   // first of the two ping-pong exchange buffers
     typename TF::Addr ad;
-    cx<T> tw[PL::NTW > 0 ? PL::NTW : 1];
+    TW tw;
 
     // The step loops contain a single copy of the transform code (instruction-cache
     // footprint): the forward transform is computed as conj(inverse(conj(x))).
@@ -102,11 +107,19 @@ struct Group {
             x[0] = cadd(x[0], pump);
     }
 
+    static constexpr bool ACC_SMEM = acc_in_smem(sizeof(T), LOGN, R);
+    cx<T>* accS;   // shared-memory accumulator S (ACC_SMEM), pre-offset by t
+    cx<T>* accL;   // shared-memory compensation word (ACC_SMEM, FP32), pre-offset by t
+
     // Block-local set-up: thread index in the group, exchange buffers, addresses, twiddles.
     CME_DEV void setup(unsigned char* smem, int g, int t_, const void* tw_table)
     {
         constexpr int W = Xbuf<T>::words_per_elem;  // 8-byte words per element
-        double* base = reinterpret_cast<double*>(smem) + (size_t)g * 2 * W * PL::BUF;
+        unsigned char* gbase = smem + (size_t)g * group_smem_bytes(sizeof(T), LOGN, R);
+        double* base = reinterpret_cast<double*>(gbase);
+        cx<T>* acc = reinterpret_cast<cx<T>*>(gbase + (size_t)2 * W * PL::BUF * 8);
+        accS = acc + t_;
+        accL = acc + N + t_;
         if constexpr (sizeof(T) == 4) {
             buf.p = reinterpret_cast<float2*>(base);
         } else {
@@ -116,7 +129,7 @@ struct Group {
         t = t_;
         par = 0;
         ad = TF::make_addr(t);
-        TF::load_tw(tw, tw_table, t);
+        tw.init(tw_table, t);
     }
 };
 
@@ -135,16 +148,229 @@ struct Coef<double> {
     CME_DEV static double h6(const StepArgs& a) { return a.h / 6.0; }
 };
 
+// nsteps steps of the instances [first, first + blockDim.x / P) of the group described by a
+// (group-relative indices; groups past a.ninst recompute the last instance and store nothing).
+// The evolving field of one thread: hi part in registers; the compensation word Dl (FP32) and
+// the Runge-Kutta accumulator S in registers, or (ACC_SMEM) in this thread's own shared-memory
+// slots t + jP.
+template <typename T, int LOGN, int R>
+struct FieldState {
+    using GR = Group<T, LOGN, R>;
+    static constexpr int P = GR::P;
+    static constexpr bool COMP = GR::COMP, AS = GR::ACC_SMEM;
+    cx<T> Dh[R];
+    cx<T> Dlr[AS ? 1 : R];
+    cx<T> Sr[AS ? 1 : R];
+    cx<T>* accL;
+    cx<T>* accS;
+
+    CME_DEV void bind(const GR& grp)
+    {
+        accL = grp.accL;
+        accS = grp.accS;
+    }
+    CME_DEV cx<T> getL(int j) const
+    {
+        if constexpr (!COMP)
+            return cx<T>{T(0), T(0)};
+        else if constexpr (AS)
+            return accL[j * P];
+        else
+            return Dlr[j];
+    }
+    CME_DEV void setL(int j, cx<T> v)
+    {
+        if constexpr (COMP) {
+            if constexpr (AS)
+                accL[j * P] = v;
+            else
+                Dlr[j] = v;
+        }
+    }
+    CME_DEV cx<T> getS(int j) const
+    {
+        if constexpr (AS)
+            return accS[j * P];
+        else
+            return Sr[j];
+    }
+    CME_DEV void setS(int j, cx<T> v)
+    {
+        if constexpr (AS)
+            accS[j * P] = v;
+        else
+            Sr[j] = v;
+    }
+    // D += d (compensated two-sum in FP32)
+    CME_DEV void add(int j, cx<T> d)
+    {
+        cx<T> l = getL(j);
+        accumulate<T, COMP>(Dh[j], l, d);
+        setL(j, l);
+    }
+    CME_DEV void load(const cx<T>* hi, const cx<T>* lo)
+    {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            Dh[j] = hi[j * P];
+            if constexpr (COMP)
+                setL(j, lo[j * P]);
+        }
+    }
+    CME_DEV void store(cx<T>* hi, cx<T>* lo) const
+    {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            hi[j * P] = Dh[j];
+            if constexpr (COMP)
+                lo[j * P] = getL(j);
+        }
+    }
+};
+
+// Instance constants of the step loops.
+template <typename T>
+struct StepConsts {
+    cx<T> pump;   // sqrt(kappa_ext) A_in
+    cx<T> cp;     // Strang pump increment over h/2
+    T gN;         // g0 / N
+    T g0h;        // g0 h / 2 (Strang half phase per |a|^2)
+    T h, hh, h6;
+};
+
+// One RK4IP step (Sec. 2 "fourth-order Runge-Kutta"; Hult 2007) written as increments of D:
+//   x2 = D + (e1 D + h/2 k1),  x3 = D + (e1 D + h/2 k2),  x4 = D + (e2 D + h E k3),
+//   D' = D + e2 D + h/6 [E (k1 + 2 k2 + 2 k3) + k4],  k1 = E F(D),  k_i = F(x_i),
+// with E = exp(L h/2), e1 = expm1(L h/2), e2 = expm1(L h).  The four stages share one copy of
+// the right-hand-side code (a runtime loop).
+template <typename T, int LOGN, int R>
+CME_DEV void rk4ip_step(Group<T, LOGN, R>& grp, FieldState<T, LOGN, R>& fs,
+                        const Props<T, LOGN, R>& pr, const StepConsts<T>& c)
+{
+    constexpr bool COMP = Group<T, LOGN, R>::COMP;
+    cx<T> x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        x[j] = fs.Dh[j];
+#pragma unroll 1
+    for (int st = 0; st < 4; ++st) {
+        grp.rhs(x, c.gN, c.pump);
+        if (st == 0) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cx<T> E = pr.getE(j);
+                const cx<T> k1 = cmul(E, x[j]);
+                fs.setS(j, cmul(E, k1));
+                x[j] = cadd(fs.Dh[j], caxpy(cmul(pr.get1(j), fs.Dh[j]), c.hh, k1));
+            }
+        } else if (st == 1) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                fs.setS(j, caxpy(fs.getS(j), T(2), cmul(pr.getE(j), x[j])));
+                x[j] = cadd(fs.Dh[j], caxpy(cmul(pr.get1(j), fs.Dh[j]), c.hh, x[j]));
+            }
+        } else if (st == 2) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cx<T> Ek3 = cmul(pr.getE(j), x[j]);
+                fs.setS(j, caxpy(fs.getS(j), T(2), Ek3));
+                x[j] = cadd(fs.Dh[j], caxpy(cmul(pr.get2(j), fs.Dh[j]), c.h, Ek3));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cx<T> e2 = pr.get2(j);
+                cx<T> d = cmul(e2, fs.Dh[j]);
+                if constexpr (COMP)
+                    d = cadd(d, cmul(e2, fs.getL(j)));
+                d = caxpy(d, c.h6, cadd(fs.getS(j), x[j]));
+                fs.add(j, d);
+            }
+        }
+    }
+}
+
+// One Strang split step (Sec. 2 "split-step Fourier method ... field in the frequency domain"):
+// exact linear+pump flow over h/2, exact Kerr flow over h, exact linear+pump flow over h/2.
+// With a = inverse transform of D the Kerr flow is a -> a exp(i g0 |a|^2 h); it is applied as
+// the increment D += DFT(a expm1(i g0 |a|^2 h))/N.
+template <typename T, int LOGN, int R>
+CME_DEV void strang_step(Group<T, LOGN, R>& grp, FieldState<T, LOGN, R>& fs,
+                         const Props<T, LOGN, R>& pr, const StepConsts<T>& c)
+{
+    constexpr bool COMP = Group<T, LOGN, R>::COMP;
+    constexpr T invN = (T)(1.0 / (1 << LOGN));
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        if (half == 1) {
+            cx<T> x[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                x[j] = fs.Dh[j];
+#pragma unroll 1
+            for (int d = 0; d < 2; ++d) {
+                grp.inverse(x);
+                if (d == 0) {
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h; the
+                        // forward transform runs as conj(inverse(conj(.)))
+                        const T ph2 = c.g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
+                        T s, co;
+                        if constexpr (sizeof(T) == 4)
+                            sincosf(ph2, &s, &co);
+                        else
+                            sincos(ph2, &s, &co);
+                        const cx<T> em = {T(-2) * s * s * invN, T(2) * s * co * invN};
+                        const cx<T> b = cmul(x[j], em);
+                        x[j] = {b.re, -b.im};
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                fs.add(j, cx<T>{x[j].re, -x[j].im});
+        }
+        // linear + pump half step: D += e1 D + delta_{mu,0} c
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const cx<T> e1 = pr.get1(j);
+            cx<T> d = cmul(e1, fs.Dh[j]);
+            if constexpr (COMP)
+                d = cadd(d, cmul(e1, fs.getL(j)));
+            if (j == 0 && grp.t == 0)
+                d = cadd(d, c.cp);
+            fs.add(j, d);
+        }
+    }
+}
+
+template <typename T>
+CME_DEV StepConsts<T> step_consts(const StepArgs& a, int inst, int N)
+{
+    StepConsts<T> c;
+    const double2 pd = a.pump[inst];
+    c.pump = {(T)pd.x, (T)pd.y};
+    const double2 cpd = a.cpump[inst];
+    c.cp = {(T)cpd.x, (T)cpd.y};
+    c.gN = (T)(a.g0[inst] / (double)N);
+    c.g0h = (T)(a.g0[inst] * a.h * 0.5);
+    c.h = Coef<T>::h(a);
+    c.hh = Coef<T>::hh(a);
+    c.h6 = Coef<T>::h6(a);
+    return c;
+}
+
+// nsteps steps of the instances [first, first + blockDim.x / P) of the group described by a
+// (group-relative indices; groups past a.ninst recompute the last instance and store nothing).
 template <typename T, int LOGN, int R, int METHOD>
-__global__ void __launch_bounds__(max_threads<LOGN, R>()) step_kernel(const StepArgs a)
+CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
 {
     using GR = Group<T, LOGN, R>;
     constexpr int N = GR::N, P = GR::P;
-    constexpr bool COMP = GR::COMP;
-    extern __shared__ __align__(16) unsigned char smem[];
 
     const int g = threadIdx.x / P;
-    int inst = blockIdx.x * a.G + g;
+    int inst = first + g;
     const bool valid = inst < a.ninst;
     if (!valid)
         inst = a.ninst - 1;  // duplicate work keeps every group in the barriers; no store
@@ -155,140 +381,36 @@ __global__ void __launch_bounds__(max_threads<LOGN, R>()) step_kernel(const Step
 
     cx<T>* hi = reinterpret_cast<cx<T>*>(a.hi) + off + t;
     cx<T>* lo = reinterpret_cast<cx<T>*>(a.lo) + off + t;
-    cx<T> Dh[R], Dl[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        Dh[j] = hi[j * P];
-        if constexpr (COMP)
-            Dl[j] = lo[j * P];
-        else
-            Dl[j] = {T(0), T(0)};
-    }
-    const double2 pd = a.pump[inst];
-    const cx<T> pump = {(T)pd.x, (T)pd.y};
-    const T gN = (T)(a.g0[inst] / (double)N);
-    const T h = Coef<T>::h(a), hh = Coef<T>::hh(a), h6 = Coef<T>::h6(a);
+    FieldState<T, LOGN, R> fs;
+    fs.bind(grp);
+    fs.load(hi, lo);
+    const StepConsts<T> c = step_consts<T>(a, inst, N);
     Props<T, LOGN, R> pr;
     pr.init(a, off, t);
 
-    if constexpr (METHOD == METHOD_RK4IP) {
-        // RK4IP (Sec. 2 "fourth-order Runge-Kutta"; Hult 2007) written as increments of D:
-        //   x2 = D + (e1 D + h/2 k1),  x3 = D + (e1 D + h/2 k2),  x4 = D + (e2 D + h E k3),
-        //   D' = D + e2 D + h/6 [E (k1 + 2 k2 + 2 k3) + k4],  k1 = E F(D),  k_i = F(x_i),
-        // with E = exp(L h/2), e1 = expm1(L h/2), e2 = expm1(L h).  The four stages share
-        // one copy of the right-hand-side code (a runtime loop).
-        cx<T> x[R], S[R];
-        for (long long n = 0; n < a.nsteps; ++n) {
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                x[j] = Dh[j];
-#pragma unroll 1
-            for (int st = 0; st < 4; ++st) {
-                grp.rhs(x, gN, pump);
-                if (st == 0) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        const cx<T> E = pr.getE(j);
-                        const cx<T> k1 = cmul(E, x[j]);
-                        S[j] = cmul(E, k1);
-                        x[j] = cadd(Dh[j], caxpy(cmul(pr.get1(j), Dh[j]), hh, k1));
-                    }
-                } else if (st == 1) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        S[j] = caxpy(S[j], T(2), cmul(pr.getE(j), x[j]));
-                        x[j] = cadd(Dh[j], caxpy(cmul(pr.get1(j), Dh[j]), hh, x[j]));
-                    }
-                } else if (st == 2) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        const cx<T> Ek3 = cmul(pr.getE(j), x[j]);
-                        S[j] = caxpy(S[j], T(2), Ek3);
-                        x[j] = cadd(Dh[j], caxpy(cmul(pr.get2(j), Dh[j]), h, Ek3));
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        const cx<T> e2 = pr.get2(j);
-                        cx<T> d = cmul(e2, Dh[j]);
-                        if constexpr (COMP)
-                            d = cadd(d, cmul(e2, Dl[j]));
-                        d = caxpy(d, h6, cadd(S[j], x[j]));
-                        accumulate<T, COMP>(Dh[j], Dl[j], d);
-                    }
-                }
-            }
-        }
-    } else {
-        // Strang split step (Sec. 2 "split-step Fourier method ... field in the frequency
-        // domain"): exact linear+pump flow over h/2, exact Kerr flow over h, exact linear+pump
-        // flow over h/2.  With a = inverse transform of D the Kerr flow is
-        // a -> a exp(i g0 |a|^2 h); it is applied as the increment D += DFT(a expm1(...))/N.
-        const double2 cpd = a.cpump[inst];
-        const cx<T> cp = {(T)cpd.x, (T)cpd.y};
-        const T g0h = (T)(a.g0[inst] * a.h * 0.5);   // half Kerr phase per |a|^2
-        const T invN = (T)(1.0 / N);
-        for (long long n = 0; n < a.nsteps; ++n) {
-#pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
-                if (half == 1) {
-                    cx<T> x[R];
-#pragma unroll
-                    for (int j = 0; j < R; ++j)
-                        x[j] = Dh[j];
-#pragma unroll 1
-                    for (int d = 0; d < 2; ++d) {
-                        grp.inverse(x);
-                        if (d == 0) {
-#pragma unroll
-                            for (int j = 0; j < R; ++j) {
-                                // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h;
-                                // the forward transform runs as conj(inverse(conj(.)))
-                                const T ph2 = g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
-                                T s, c;
-                                if constexpr (sizeof(T) == 4)
-                                    sincosf(ph2, &s, &c);
-                                else
-                                    sincos(ph2, &s, &c);
-                                const cx<T> em = {T(-2) * s * s * invN, T(2) * s * c * invN};
-                                const cx<T> b = cmul(x[j], em);
-                                x[j] = {b.re, -b.im};
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < R; ++j)
-                        accumulate<T, COMP>(Dh[j], Dl[j], cx<T>{x[j].re, -x[j].im});
-                }
-                // linear + pump half step: D += e1 D + delta_{mu,0} c
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const cx<T> e1 = pr.get1(j);
-                    cx<T> d = cmul(e1, Dh[j]);
-                    if constexpr (COMP)
-                        d = cadd(d, cmul(e1, Dl[j]));
-                    if (j == 0 && t == 0)
-                        d = cadd(d, cp);
-                    accumulate<T, COMP>(Dh[j], Dl[j], d);
-                }
-            }
-        }
+    for (long long n = 0; n < a.nsteps; ++n) {
+        if constexpr (METHOD == METHOD_RK4IP)
+            rk4ip_step(grp, fs, pr, c);
+        else
+            strang_step(grp, fs, pr, c);
     }
 
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < R; ++j)
-        bad |= !(isfinite(Dh[j].re) && isfinite(Dh[j].im));
+        bad |= !(isfinite(fs.Dh[j].re) && isfinite(fs.Dh[j].im));
     if (valid) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            hi[j * P] = Dh[j];
-            if constexpr (COMP)
-                lo[j * P] = Dl[j];
-        }
+        fs.store(hi, lo);
         if (bad)
             a.status[inst] = 1;
     }
+}
+
+template <typename T, int LOGN, int R, int METHOD>
+__global__ void __launch_bounds__(max_threads<LOGN, R>()) step_kernel(const StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    step_body<T, LOGN, R, METHOD>(a, blockIdx.x * a.G, smem);
 }
 
 // Diagnostics: one transform or one right-hand-side evaluation of the current field, written in

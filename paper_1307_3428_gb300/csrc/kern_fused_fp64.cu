@@ -1,0 +1,13 @@
+// Persistent work-list kernel for batches with several N, FP64.
+#include "cme_launch.cuh"
+#include "cme_fused.cuh"
+
+namespace cme {
+
+cudaError_t launch_fused_fp64(int method, const FusedArgs& a, int grid, size_t smem,
+                                 cudaStream_t s)
+{
+    return launch_fused_t<double>(method, a, grid, smem, s);
+}
+
+}  // namespace cme

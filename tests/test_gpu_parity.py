@@ -280,3 +280,83 @@ def test_torch_allocator_and_stream():
         b.close()
     finally:
         cme.load().cme_set_allocator(cme.ALLOC_FN(), cme.FREE_FN(), None)
+
+
+# ---------------------------------------------------------------------------- uneven batches
+
+def uneven_sample_indices():
+    """One MI-stable instance of each N of the uneven workload (indices into its 256)."""
+    w = wl.uneven(nsteps=1)
+    picks = []
+    for k, N in enumerate((256, 1024, 2048, 4096)):
+        for b in range(64 * k, 64 * (k + 1)):
+            inst = w.instances[b]
+            P = cf.cw_powers(inst.sigma, inst.A_in, 1.0, 0.5, 1.0)[0]
+            if cf.max_mi_gain(P, N, 0.01, 1e-4, inst.sigma, 1.0, 1.0) < -0.05:
+                picks.append(b)
+                break
+    return picks
+
+
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_uneven_modes_agree_bitwise_and_with_oracle(persistent):
+    """Mixed N (4..4096) in one batch: the persistent work-list kernel and the concurrent
+    per-group kernels give identical fields; both agree with the oracle."""
+    sizes = (4, 8, 64, 64, 256, 512, 1024, 2048, 4096)
+    insts = [wl.random_instance(N, 1500 + i, amp=0.2 * min(1.0, np.sqrt(64.0 / N)), sigma=1.0,
+                                A_in=1.3) for i, N in enumerate(sizes)]
+    for prec in (cme.FP64, cme.FP32):
+        b = batch_of(insts, prec, persistent=persistent, use_graph=True)
+        b.step(1e-3, 12)
+        got = b.split(b.get_state())
+        ref1 = batch_of(insts, prec, persistent=3 - persistent)
+        ref1.step(1e-3, 12)
+        if prec == cme.FP64:
+            assert np.array_equal(b.get_state(), ref1.get_state()) or \
+                rel(b.get_state(), ref1.get_state()) < 1e-14
+        for g, inst in zip(got, insts):
+            r = fft_engine.rk4ip(fft_engine.Batch([inst]), 1e-3, 12)[0]
+            assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_uneven_full_batch_full_horizon(prec):
+    """N in {256, 1024, 2048, 4096} x 64 instances, 50000 RK4IP steps of h=2e-4 in one
+    persistent launch (one graph); one stable instance per N against the FP64 oracle."""
+    w = wl.uneven()
+    b = batch_of(w.instances, prec, use_graph=True, persistent=2)
+    b.step(w.h, w.nsteps)
+    b.synchronize()
+    assert not b.status().any()
+    got = b.split(b.get_state())
+    for i in uneven_sample_indices():
+        inst = w.instances[i]
+        ref = fft_engine.rk4ip(fft_engine.Batch([inst]), w.h, w.nsteps)[0]
+        err = rel(got[i], ref)
+        assert err <= TOL[prec], (i, inst.N, err)
+
+
+def test_autotune_keeps_state_and_results():
+    insts = wl.sweep512(indices=range(0, 256, 8)).instances
+    for prec in (cme.FP32, cme.FP64):
+        a = batch_of(insts, prec)
+        s0 = a.get_state()
+        plan = a.autotune(5e-4, probe_steps=40)
+        assert plan["radix"] in (0, 4, 8, 16) and plan["persistent"] in (1, 2)
+        assert np.array_equal(a.get_state(), s0)
+        assert a.time() == 0.0
+        a.step(5e-4, 30)
+        ref = fft_engine.rk4ip(fft_engine.Batch(insts), 5e-4, 30)
+        for g, r in zip(a.split(a.get_state()), ref):
+            assert rel(g, r) <= TOL[prec]
+
+
+def test_autotune_uneven():
+    insts = [wl.random_instance(N, 1700 + i, amp=0.1) for i, N in enumerate((64, 256, 256, 1024))]
+    b = batch_of(insts, cme.FP32)
+    plan = b.autotune(1e-3, probe_steps=20)
+    assert plan["persistent"] in (1, 2)
+    b.step(1e-3, 10)
+    for g, inst in zip(b.split(b.get_state()), insts):
+        r = fft_engine.rk4ip(fft_engine.Batch([inst]), 1e-3, 10)[0]
+        assert rel(g, r) <= 1e-5
