@@ -193,6 +193,36 @@ int cme_transform(cme_batch b, int sign, double* out, int where);
  * field, FWM through Eq. 4 on the device (centred order, 2 * total_modes doubles). */
 int cme_eval_rhs(cme_batch b, double* out, int where);
 
+/* ---- integration without device allocation ------------------------------------------- */
+
+/* Size of the device array that cme_rk4ip_noalloc uses for all of its scratch memory. */
+#define CME_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers that may not
+ * allocate device memory themselves -- for example an application whose device memory all comes
+ * from its own fixed-size pool, or code running between other asynchronous work where
+ * cudaMalloc, which can synchronise the whole device, must not be called.
+ *
+ * Advances `count` instances of N modes (power of two in [4, 4096]) by nsteps RK4IP steps of
+ * size h in FP64, in place, with the same kernels as cme_step on an FP64 RK4IP batch, and
+ * calls no cudaMalloc, cudaFree or allocating library routine.  All pointers are device memory
+ * owned by the caller:
+ *   d_kappa, d_omega  N * count doubles each: kappa_mu and omega_mu per instance, centred;
+ *   d_inst            5 * count doubles: (g0, kappa_ext, Re A_in, Im A_in, sigma) per instance;
+ *   d_field           2 * N * count doubles (in/out): rotating-frame field, interleaved, centred.
+ * Work is enqueued on cuda_stream (NULL: the legacy default stream) and the call returns without
+ * waiting.  Scratch: one static device array of CME_NOALLOC_SCRATCH_BYTES (16 MiB), held by
+ * every GPU that loads the library until the process exits; it needs about 84 bytes per mode
+ * plus 16 N, so at most about 190000 modes per call -- larger sets are rejected with
+ * CME_ERR_INVALID_ARG.  Every call shares that array and it keeps the previous call's
+ * contents (the status words are cleared by each call): calls that overlap on the GPU, on
+ * different streams or from different threads, race and corrupt each other.  The first call on
+ * a device takes the array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture.  Errors: UNSUPPORTED_N, INVALID_ARG, CUDA. */
+int cme_rk4ip_noalloc(int N, int count, double h, long nsteps, const double* d_kappa,
+                      const double* d_omega, const double* d_inst, double* d_field,
+                      void* cuda_stream);
+
 /* ---- library ------------------------------------------------------------------------ */
 
 /* Device allocation hooks used by every later batch: alloc(bytes, ctx) returns device memory

@@ -85,6 +85,8 @@ _SIGS = [
     ("cme_status", ctypes.c_int, [_VP, _IP]),
     ("cme_grad", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long, _DP, ctypes.c_double,
                                 ctypes.c_long, ctypes.POINTER(Grads)]),
+    ("cme_rk4ip_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_long, _VP, _VP, _VP, _VP, _VP]),
     ("cme_transform", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int]),
     ("cme_eval_rhs", ctypes.c_int, [_VP, _DP, ctypes.c_int]),
     ("cme_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, _VP]),
@@ -309,6 +311,14 @@ class Batch:
         out = np.empty(2 * self.total, dtype=np.float64)
         _check(load().cme_eval_rhs(self.handle, _dptr(out), HOST))
         return out.view(np.complex128)
+
+
+def rk4ip_noalloc(N: int, count: int, h: float, nsteps: int, d_kappa: int, d_omega: int,
+                  d_inst: int, d_field: int, stream: int = 0):
+    """cme_rk4ip_noalloc on device pointers supplied by the caller (no device allocation by
+    the library; see include/cme.h for the 16 MiB scratch limit and the sharing rules)."""
+    _check(load().cme_rk4ip_noalloc(int(N), int(count), float(h), int(nsteps), d_kappa,
+                                    d_omega, d_inst, d_field, stream or None))
 
 
 def fma_peak(precision=FP32) -> float:

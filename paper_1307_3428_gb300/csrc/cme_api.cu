@@ -41,6 +41,21 @@ int fail(int code, const char* fmt, ...)
     return code;
 }
 
+}  // namespace
+
+int cme::report_error(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+namespace {
+
 int cuda_fail(cudaError_t e, const char* what)
 {
     return fail(e == cudaErrorMemoryAllocation ? CME_ERR_OOM : CME_ERR_CUDA, "%s: %s (%s)", what,

@@ -55,6 +55,9 @@ cudaError_t launch_step_fp32_strang(int logN, int R, const StepArgs& a, cudaStre
 cudaError_t launch_diag_fp64(int logN, int R, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_diag_fp32(int logN, int R, const StepArgs& a, cudaStream_t s);
 
+// Record an error message for cme_last_error() and return `code` (cme_api.cu).
+int report_error(int code, const char* fmt, ...);
+
 // Auxiliary kernels (aux_kernels.cu).
 struct PropArgs {
     int total;                // modes in the batch
