@@ -220,6 +220,8 @@ def run_gpu(args, world, rank, local):
         w = wl.uneven()
     elif args.workload == "plain64":
         w = wl.plain64()
+    elif args.workload == "octave":
+        w = wl.octave()
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     headline = args.workload == "sweep512"
@@ -425,7 +427,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--radix", type=int, default=0, help="field values per thread (0: default)")
     ap.add_argument("--inst-per-cta", type=int, default=0, help="instances per block (0: default)")
-    ap.add_argument("--workload", default="sweep512", choices=["sweep512", "uneven", "plain64"],
+    ap.add_argument("--workload", default="sweep512",
+                    choices=["sweep512", "uneven", "plain64", "octave"],
                     help="sweep512 is the headline workload; the others are secondary records")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--autotune", action="store_true")

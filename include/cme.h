@@ -37,7 +37,7 @@ extern "C" {
 /* ---- status codes ------------------------------------------------------------------- */
 #define CME_OK 0
 #define CME_ERR_INVALID_ARG (-1)   /* null pointer, bad count, h or nsteps out of range */
-#define CME_ERR_UNSUPPORTED_N (-2) /* N not a power of two in [4, 4096] */
+#define CME_ERR_UNSUPPORTED_N (-2) /* N not a power of two in [4, 2^20] */
 #define CME_ERR_CUDA (-3)          /* a CUDA runtime call failed; message has the CUDA error */
 #define CME_ERR_NONFINITE (-4)     /* a field value became NaN or Inf (see cme_status) */
 #define CME_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
@@ -80,7 +80,9 @@ void cme_default_options(cme_options* opt);
 /* ---- instances (host-side parameter sets) -------------------------------------------- */
 
 /* Create one CME problem (Eq. 1 parameters, Sec. 2).
- *   N          number of modes, power of two in [4, 4096];
+ *   N          number of modes, power of two in [4, 2^20]; N <= 4096 runs one instance per
+ *              thread group with the field on chip, larger N (RK4IP only, no cme_grad) runs
+ *              the four-step split N = N1 N2 through row and column kernels;
  *   kappa_mu   N total losses (centred order), each >= 0;
  *   omega_mu   N cold-cavity resonance frequencies (centred order); only differences to
  *              omega_0 enter the model;
@@ -98,8 +100,9 @@ void cme_destroy(cme_instance inst);
 
 /* ---- batches (device-resident sets of instances) --------------------------------------- */
 
-/* Build a batch from `count` instances (copied; the instances may be destroyed afterwards).
- * Instances may differ in N; each distinct N forms its own launch group.  `cuda_stream` is a
+/* Build a batch from `count` instances (copied; the instances may be destroyed afterwards),
+ * given in non-decreasing N.  Instances may differ in N; each distinct N forms its own launch
+ * group.  `cuda_stream` is a
  * cudaStream_t; NULL makes the batch create and own a non-blocking stream.  The field starts
  * at the instances' initial fields, tau = 0.  Errors: INVALID_ARG, UNSUPPORTED_N, CUDA, OOM. */
 int cme_batch_create(const cme_instance* v, int count, const cme_options* opt,

@@ -17,6 +17,7 @@
 #include "cme.h"
 #include "cme_internal.h"
 #include "cme_adjoint_args.h"
+#include "cme_large.cuh"
 
 using namespace cme;
 
@@ -132,7 +133,15 @@ struct LaunchGroup {
     int first = 0, count = 0;   // instances [first, first+count)
     long long base = 0;         // first mode offset
     int R = 8, G = 1;
+    // N > 4096: four-step split N = N1 N2 (column length N1, row length N2)
+    bool large = false;
+    int logN1 = 0, logN2 = 0, G1 = 1, G2 = 1;
+    void* Y = nullptr;          // [count][N] inter-pass buffers
+    void* Z = nullptr;
+    cudaGraphExec_t chunk = nullptr;   // LARGE_CHUNK steps, replayed by cme_step
+    double chunk_h = 0.0;
 };
+constexpr int LARGE_CHUNK = 32;
 }  // namespace
 
 struct cme_batch_s {
@@ -192,7 +201,20 @@ struct cme_batch_s {
         for (auto& kv : graphs)
             cudaGraphExecDestroy(kv.second.first);
         graphs.clear();
+        for (auto& g : groups) {
+            if (g.chunk)
+                cudaGraphExecDestroy(g.chunk);
+            g.chunk = nullptr;
+        }
     }
+    bool has_large() const
+    {
+        for (auto& g : groups)
+            if (g.large)
+                return true;
+        return false;
+    }
+    void* S_large = nullptr;   // Runge-Kutta accumulator of four-step groups (per mode)
 
     void* alloc(size_t bytes)
     {
@@ -212,7 +234,19 @@ int plan_batch(cme_batch b, const cme_options& o)
     if (o.steps_per_launch < 0 || o.inst_per_cta < 0 || o.radix < 0 || o.persistent < 0 ||
         o.persistent > 2)
         return fail(CME_ERR_INVALID_ARG, "launch plan: invalid option");
+    bool any_large = false;
     for (auto& g : b->groups) {
+        if (g.large) {
+            // rows of N2 and columns of N1 values, 8 per thread; whole warps per block
+            auto blocks_of = [](int len) {
+                const int P = len / 8;
+                return P >= 64 ? 1 : std::max(1, 64 / P);
+            };
+            g.G1 = blocks_of(1 << g.logN1);
+            g.G2 = blocks_of(1 << g.logN2);
+            any_large = true;
+            continue;
+        }
         int R = o.radix ? o.radix : default_radix(g.logN);
         if (R > g.N)
             R = g.N;
@@ -240,6 +274,8 @@ int plan_batch(cme_batch b, const cme_options& o)
     int mode = o.persistent;
     if (mode == 0)
         mode = b->groups.size() > 1 ? 2 : 1;
+    if (any_large)
+        mode = 1;   // four-step groups run their own kernel sequence
     if (mode == 2) {
         // tiles of 256 / P instances (the fused kernel's own values per thread), heaviest first;
         // a tile's time scales with R log2 N
@@ -307,8 +343,8 @@ int cme_create(int N, const double* kappa_mu, const double* omega_mu, double g0,
     if (!out)
         return fail(CME_ERR_INVALID_ARG, "cme_create: out is NULL");
     *out = nullptr;
-    if (!is_pow2(N) || N < 4 || N > 4096)
-        return fail(CME_ERR_UNSUPPORTED_N, "cme_create: N=%d is not a power of two in [4, 4096]", N);
+    if (!is_pow2(N) || N < 4 || N > (1 << 20))
+        return fail(CME_ERR_UNSUPPORTED_N, "cme_create: N=%d is not a power of two in [4, 2^20]", N);
     if (!kappa_mu || !omega_mu)
         return fail(CME_ERR_INVALID_ARG, "cme_create: kappa_mu and omega_mu are required");
     for (int i = 0; i < N; ++i) {
@@ -432,6 +468,11 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         g.first = i;
         g.count = j - i;
         g.base = b->off_h[i];
+        if (g.logN > 12) {
+            g.large = true;
+            g.logN1 = (g.logN + 1) / 2;
+            g.logN2 = g.logN / 2;
+        }
         b->groups.push_back(g);
         i = j;
     }
@@ -442,6 +483,14 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     }
     // host-side validation of the launch options before any CUDA call
     for (auto& g : b->groups) {
+        if (g.large) {
+            if (o.integrator != CME_RK4IP) {
+                cme_batch_destroy(b);
+                return fail(CME_ERR_INVALID_ARG,
+                            "cme_batch_create: N=%d > 4096 runs RK4IP only", g.N);
+            }
+            continue;
+        }
         const int R = std::min(o.radix ? o.radix : default_radix(g.logN), g.N);
         if (!shape_compiled(g.logN, R) || o.persistent < 0 || o.persistent > 2) {
             cme_batch_destroy(b);
@@ -489,6 +538,16 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     for (auto& g : b->groups) {
         if (!b->tw.count(g.logN))
             b->tw[g.logN] = A((size_t)g.N * b->elem);
+        if (g.large) {
+            if (!b->tw.count(g.logN1))
+                b->tw[g.logN1] = A((size_t)(1 << g.logN1) * b->elem);
+            if (!b->tw.count(g.logN2))
+                b->tw[g.logN2] = A((size_t)(1 << g.logN2) * b->elem);
+            g.Y = A((size_t)g.count * g.N * b->elem);
+            g.Z = A((size_t)g.count * g.N * b->elem);
+            if (!b->S_large)
+                b->S_large = A(T * b->elem);
+        }
     }
     b->tiles_d = (FusedTile*)A(count * sizeof(FusedTile));
     b->counter_d = (int*)A(64);
@@ -632,9 +691,12 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
     return a;
 }
 
-cudaError_t launch_group_step(cme_batch b, const LaunchGroup& g, long long nsteps,
-                              cudaStream_t st)
+cudaError_t large_steps(cme_batch b, LaunchGroup& g, long long nsteps, cudaStream_t st);
+
+cudaError_t launch_group_step(cme_batch b, LaunchGroup& g, long long nsteps, cudaStream_t st)
 {
+    if (g.large)
+        return large_steps(b, g, nsteps, st);
     StepArgs a = group_args(b, g);
     a.nsteps = nsteps;
     ++g_launches;
@@ -643,6 +705,122 @@ cudaError_t launch_group_step(cme_batch b, const LaunchGroup& g, long long nstep
                                          : launch_step_fp64_strang(g.logN, g.R, a, st);
     return b->method == METHOD_RK4IP ? launch_step_fp32_rk4ip(g.logN, g.R, a, st)
                                      : launch_step_fp32_strang(g.logN, g.R, a, st);
+}
+
+LargeArgs large_args(cme_batch b, const LaunchGroup& g)
+{
+    LargeArgs a{};
+    a.ninst = g.count;
+    a.logN1 = g.logN1;
+    a.logN2 = g.logN2;
+    a.base = g.base;
+    a.hi = b->hi;
+    a.lo = b->lo;
+    a.S = b->S_large;
+    a.Y = g.Y;
+    a.Z = g.Z;
+    a.E = b->E;
+    a.e1 = b->e1;
+    a.e2 = b->e2;
+    a.twN = b->tw.at(g.logN);
+    a.tw1 = b->tw.at(g.logN1);
+    a.tw2 = b->tw.at(g.logN2);
+    a.pump = b->pump_d + g.first;
+    a.g0 = b->g0_d + g.first;
+    a.status = b->status_d + g.first;
+    a.h = b->h_cur;
+    a.hf = (float)b->h_cur;
+    a.hhf = (float)(0.5 * b->h_cur);
+    a.h6f = (float)(b->h_cur / 6.0);
+    return a;
+}
+
+cudaError_t large_row(cme_batch b, const LaunchGroup& g, LargeArgs a, cudaStream_t st)
+{
+    a.G = g.G2;
+    ++g_launches;
+    const long long rows = (long long)g.count << g.logN1;
+    return b->prec == PREC_FP64 ? launch_large_row_fp64(g.logN2, a, rows, st)
+                                : launch_large_row_fp32(g.logN2, a, rows, st);
+}
+
+cudaError_t large_col(cme_batch b, const LaunchGroup& g, LargeArgs a, int stage, cudaStream_t st)
+{
+    a.G = g.G1;
+    a.stage = stage;
+    ++g_launches;
+    const long long cols = (long long)g.count << g.logN2;
+    return b->prec == PREC_FP64 ? launch_large_col_fp64(g.logN1, a, cols, st)
+                                : launch_large_col_fp32(g.logN1, a, cols, st);
+}
+
+// One RK4IP step of a four-step group: [row, col] for each of the four stages; the last column
+// pass also transforms the new field for the next step's first stage.
+cudaError_t large_one_step(cme_batch b, const LaunchGroup& g, const LargeArgs& a, cudaStream_t st)
+{
+    for (int stage = 0; stage < 4; ++stage) {
+        cudaError_t e = large_row(b, g, a, st);
+        if (e == cudaSuccess)
+            e = large_col(b, g, a, stage, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// nsteps RK4IP steps of a four-step group: a start column pass, then whole chunks of
+// LARGE_CHUNK steps replayed from a captured graph, then the remainder launched directly.
+cudaError_t large_steps(cme_batch b, LaunchGroup& g, long long nsteps, cudaStream_t st)
+{
+    const LargeArgs a = large_args(b, g);
+    cudaError_t e = large_col(b, g, a, LARGE_START, st);
+    if (e != cudaSuccess)
+        return e;
+    const long long chunks = nsteps / LARGE_CHUNK;
+    long long rest = nsteps % LARGE_CHUNK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess)
+        return e;
+    if (chunks > 0 && cap == cudaStreamCaptureStatusNone) {
+        if (!g.chunk || g.chunk_h != b->h_cur) {
+            if (g.chunk)
+                cudaGraphExecDestroy(g.chunk);
+            g.chunk = nullptr;
+            cudaGraph_t graph;
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess)
+                return e;
+            const long before = g_launches.load();
+            for (int k = 0; k < LARGE_CHUNK && e == cudaSuccess; ++k)
+                e = large_one_step(b, g, a, st);
+            g_launches.store(before);
+            cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+            if (e != cudaSuccess)
+                return e;
+            if (e2 != cudaSuccess)
+                return e2;
+            e = cudaGraphInstantiate(&g.chunk, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess)
+                return e;
+            g.chunk_h = b->h_cur;
+        }
+        for (long long c = 0; c < chunks; ++c) {
+            g_launches += 8 * LARGE_CHUNK;
+            e = cudaGraphLaunch(g.chunk, st);
+            if (e != cudaSuccess)
+                return e;
+        }
+    } else {
+        rest = nsteps;
+    }
+    for (long long k = 0; k < rest; ++k) {
+        e = large_one_step(b, g, a, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 // Dynamic shared memory of the work-list kernel: the largest tile, with every group's layout
@@ -764,7 +942,7 @@ int cme_step(cme_batch b, double h, long nsteps)
     int rc = ensure_propagators(b, h);
     if (rc)
         return rc;
-    if (b->opt.use_graph) {
+    if (b->opt.use_graph && !b->has_large()) {
         auto key = std::make_pair(h, nsteps);
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
@@ -863,6 +1041,11 @@ int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out)
 {
     if (!b || !(h > 0.0) || !std::isfinite(h) || probe_steps <= 0)
         return fail(CME_ERR_INVALID_ARG, "cme_autotune: invalid argument");
+    if (b->has_large()) {   // four-step groups have a single launch plan
+        if (plan_out)
+            *plan_out = b->opt;
+        return CME_OK;
+    }
     const std::string key = tune_key(b, h);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1145,6 +1328,25 @@ int run_diag(cme_batch b, int mode, double* out, int where, int reorder_centred,
     if (!b || !out || (where != CME_HOST && where != CME_DEVICE))
         return fail(CME_ERR_INVALID_ARG, "%s: invalid argument", who);
     for (auto& g : b->groups) {
+        if (g.large) {
+            if (mode == DIAG_DFT)
+                return fail(CME_ERR_INVALID_ARG, "%s: sign -1 is not available for N > 4096", who);
+            LargeArgs la = large_args(b, g);
+            la.diag_out = b->diag;
+            cudaError_t e = large_col(b, g, la, LARGE_START, b->stream);
+            if (e == cudaSuccess && mode == DIAG_IDFT) {
+                la.diag = LDIAG_IDFT;
+                e = large_row(b, g, la, b->stream);
+            } else if (e == cudaSuccess) {
+                e = large_row(b, g, la, b->stream);
+                la.diag = LDIAG_RHS;
+                if (e == cudaSuccess)
+                    e = large_col(b, g, la, 0, b->stream);
+            }
+            if (e != cudaSuccess)
+                return cuda_fail(e, who);
+            continue;
+        }
         StepArgs a = group_args(b, g);
         a.diag_mode = mode;
         a.diag_out = b->diag;
@@ -1248,6 +1450,8 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
         return fail(CME_ERR_INVALID_ARG, "cme_grad: invalid argument");
     if (b->method != METHOD_RK4IP)
         return fail(CME_ERR_INVALID_ARG, "cme_grad: gradients are implemented for RK4IP batches");
+    if (b->has_large())
+        return fail(CME_ERR_INVALID_ARG, "cme_grad: gradients are implemented for N <= 4096");
     const long long K = segment ? segment : (long long)std::ceil(std::sqrt((double)nsteps));
     const long long S = (nsteps + K - 1) / K;
     int rc = ensure_grad_scratch(b, S, K);

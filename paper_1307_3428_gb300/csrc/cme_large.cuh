@@ -1,0 +1,231 @@
+// Large-N RK4IP (N = N1 N2 > 4096): the transforms over the mode number are split into
+// N2 column transforms of length N1 and N1 row transforms of length N2 (the four-step
+// factorisation of the DFT), each done by one thread group with the in-block transform code.
+//
+// Index maps (transform order m = mu mod N, time index j):
+//     m = m1 N2 + m2,   j = j1 + N1 j2.
+// Inverse transform a_j = sum_m x_m exp(+2 pi i j m / N):
+//     Y[j1][m2] = exp(+2 pi i j1 m2 / N) sum_m1 x[m1 N2 + m2] exp(+2 pi i j1 m1 / N1)   (col)
+//     a[j1 + N1 j2] = sum_m2 Y[j1][m2] exp(+2 pi i j2 m2 / N2)                         (row)
+// Forward transform X_m = sum_j b_j exp(-2 pi i j m / N):
+//     Z[j1][m2] = exp(-2 pi i j1 m2 / N) sum_j2 b[j1 + N1 j2] exp(-2 pi i j2 m2 / N2)   (row)
+//     X[m1 N2 + m2] = sum_j1 Z[j1][m2] exp(-2 pi i j1 m1 / N1)                         (col)
+// One RK stage is therefore two kernels:
+//   row: load Y row j1, inverse over m2, Kerr term (i g0/N) |a|^2 a, forward over j2,
+//        twiddle, store Z row j1 (the time-domain field never leaves registers);
+//   col: load Z column m2, forward over j1, pump, Runge-Kutta combination of the stage (the
+//        same increment form as the in-block kernels), inverse over m1 of the next stage's
+//        input, twiddle, store Y column m2.
+// The field, the accumulator S and the propagators stay in HBM (L2-resident at these sizes);
+// Y and Z are the inter-pass buffers (scratch).
+#pragma once
+
+#include "cme_step.cuh"
+
+namespace cme {
+
+enum { LARGE_START = -1, LARGE_FINAL = 4 };
+enum { LDIAG_NONE = 0, LDIAG_IDFT = 1, LDIAG_RHS = 2 };
+
+struct LargeArgs {
+    int ninst;
+    int logN1, logN2;        // column transform length N1 = 2^logN1, row length N2 = 2^logN2
+    int G;                   // thread groups (rows or columns) per block
+    long long base;          // first mode offset of the group
+    void* hi;                // field (FP32: hi part)
+    void* lo;                // FP32 compensation word
+    void* S;                 // Runge-Kutta accumulator
+    void* Y;                 // [ninst][N1][N2] column-pass output
+    void* Z;                 // [ninst][N1][N2] row-pass output
+    const void* E;
+    const void* e1;
+    const void* e2;
+    const void* twN;         // exp(2 pi i k / N), k < N
+    const void* tw1;         // exp(2 pi i k / N1)
+    const void* tw2;         // exp(2 pi i k / N2)
+    const double2* pump;     // per instance (group-relative)
+    const double* g0;
+    int* status;
+    double h;
+    float hf, hhf, h6f;
+    int stage;               // col kernel: LARGE_START, 0..3, LARGE_FINAL
+    int diag;                // LDIAG_*: write to diag_out instead of continuing
+    void* diag_out;          // [ninst][N] transform order (rhs) or time order (idft)
+};
+
+// Row pass: instance i = row / N1, row j1 = row mod N1.
+template <typename T, int LOGN2, int R>
+__global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(const LargeArgs A)
+{
+    using GR = Group<T, LOGN2, R>;
+    constexpr int N2 = GR::N, P = GR::P;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N1 = 1 << A.logN1;
+    const long long N = (long long)N1 * N2;
+    const int g = threadIdx.x / P;
+    const long long rows = (long long)A.ninst * N1;
+    long long row = (long long)blockIdx.x * A.G + g;
+    const bool valid = row < rows;
+    if (!valid)
+        row = rows - 1;
+    const int inst = (int)(row / N1);
+    const int j1 = (int)(row - (long long)inst * N1);
+    GR grp;
+    grp.setup(smem, g, threadIdx.x - g * P, A.tw2);
+    const int t = grp.t;
+    const long long ibase = (long long)inst * N;   // offset of this instance in Y / Z
+    const cx<T>* yrow = reinterpret_cast<const cx<T>*>(A.Y) + ibase + (long long)j1 * N2 + t;
+    cx<T> x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        x[j] = yrow[j * P];
+    if (A.diag == LDIAG_IDFT) {
+        grp.inverse(x);
+        if (valid) {
+            cx<T>* d = reinterpret_cast<cx<T>*>(A.diag_out) + A.base + ibase + j1;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                d[(long long)(t + j * P) * N1] = x[j];   // a[j1 + N1 j2], j2 = t + jP
+        }
+        return;
+    }
+    const T gN = (T)(A.g0[inst] / (double)N);
+    grp.rhs(x, gN, cx<T>{T(0), T(0)});   // forward(i g0/N |a|^2 a) over j2, natural m2
+    cx<T>* zrow = reinterpret_cast<cx<T>*>(A.Z) + ibase + (long long)j1 * N2 + t;
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int m2 = t + j * P;
+            const cx<T> w = gload<T>(A.twN, ((long long)j1 * m2) & (N - 1));
+            zrow[j * P] = cmulc(x[j], w);        // * exp(-2 pi i j1 m2 / N)
+        }
+    }
+}
+
+// Column pass: instance i = col / N2, column m2 = col mod N2.
+template <typename T, int LOGN1, int R>
+__global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(const LargeArgs A)
+{
+    using GR = Group<T, LOGN1, R>;
+    constexpr int N1 = GR::N, P = GR::P;
+    constexpr bool COMP = GR::COMP;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N2 = 1 << A.logN2;
+    const long long N = (long long)N1 * N2;
+    const int g = threadIdx.x / P;
+    const long long cols = (long long)A.ninst * N2;
+    long long col = (long long)blockIdx.x * A.G + g;
+    const bool valid = col < cols;
+    if (!valid)
+        col = cols - 1;
+    const int inst = (int)(col / N2);
+    const int m2 = (int)(col - (long long)inst * N2);
+    GR grp;
+    grp.setup(smem, g, threadIdx.x - g * P, A.tw1);
+    const int t = grp.t;
+    const long long ibase = (long long)inst * N;
+    // element j of this thread: row / mode index m1 = t + jP  ->  offset m1 N2 + m2
+    const long long e0 = ibase + (long long)t * N2 + m2;
+    const long long estride = (long long)P * N2;
+    const long long f0 = A.base + e0;   // same element in the field / per-mode arrays
+
+    cx<T> x[R];
+    if (A.stage != LARGE_START) {
+        // forward transform over j1 of Z column m2, as conj(inverse(conj(.)))
+        const cx<T>* z = reinterpret_cast<const cx<T>*>(A.Z) + e0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const cx<T> v = z[j * estride];
+            x[j] = {v.re, -v.im};
+        }
+        grp.inverse(x);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            x[j].im = -x[j].im;
+        if (t == 0 && m2 == 0) {
+            const double2 pd = A.pump[inst];
+            x[0] = cadd(x[0], cx<T>{(T)pd.x, (T)pd.y});
+        }
+        if (A.diag == LDIAG_RHS) {
+            if (valid) {
+                cx<T>* d = reinterpret_cast<cx<T>*>(A.diag_out) + f0;
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    d[j * estride] = x[j];
+            }
+            return;
+        }
+    }
+    cx<T>* hi = reinterpret_cast<cx<T>*>(A.hi) + f0;
+    cx<T>* lo = reinterpret_cast<cx<T>*>(A.lo) + f0;
+    cx<T>* Sp = reinterpret_cast<cx<T>*>(A.S) + f0;
+    const cx<T>* Ep = reinterpret_cast<const cx<T>*>(A.E) + f0;
+    const cx<T>* e1p = reinterpret_cast<const cx<T>*>(A.e1) + f0;
+    const cx<T>* e2p = reinterpret_cast<const cx<T>*>(A.e2) + f0;
+    T h, hh, h6;
+    if constexpr (sizeof(T) == 4) {
+        h = A.hf;
+        hh = A.hhf;
+        h6 = A.h6f;
+    } else {
+        h = A.h;
+        hh = 0.5 * A.h;
+        h6 = A.h / 6.0;
+    }
+    const int st = A.stage;
+    // Runge-Kutta combination of stage st (same increment form as rk4ip_step) and the next
+    // stage's input; LARGE_START only loads D, LARGE_FINAL finishes the step without going on.
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const long long o = j * estride;
+        cx<T> Dh = hi[o];
+        if (st == LARGE_START) {
+            x[j] = Dh;
+        } else if (st == 0) {
+            const cx<T> E = gload<T>(Ep, o);
+            const cx<T> k1 = cmul(E, x[j]);
+            Sp[o] = cmul(E, k1);
+            x[j] = cadd(Dh, caxpy(cmul(gload<T>(e1p, o), Dh), hh, k1));
+        } else if (st == 1) {
+            Sp[o] = caxpy(Sp[o], T(2), cmul(gload<T>(Ep, o), x[j]));
+            x[j] = cadd(Dh, caxpy(cmul(gload<T>(e1p, o), Dh), hh, x[j]));
+        } else if (st == 2) {
+            const cx<T> Ek3 = cmul(gload<T>(Ep, o), x[j]);
+            Sp[o] = caxpy(Sp[o], T(2), Ek3);
+            x[j] = cadd(Dh, caxpy(cmul(gload<T>(e2p, o), Dh), h, Ek3));
+        } else {
+            const cx<T> e2 = gload<T>(e2p, o);
+            cx<T> Dl = {T(0), T(0)};
+            if constexpr (COMP)
+                Dl = lo[o];
+            cx<T> d = cmul(e2, Dh);
+            if constexpr (COMP)
+                d = cadd(d, cmul(e2, Dl));
+            d = caxpy(d, h6, cadd(Sp[o], x[j]));
+            accumulate<T, COMP>(Dh, Dl, d);
+            if (valid) {
+                hi[o] = Dh;
+                if constexpr (COMP)
+                    lo[o] = Dl;
+                if (!(isfinite(Dh.re) && isfinite(Dh.im)))
+                    A.status[inst] = 1;
+            }
+            x[j] = Dh;
+        }
+    }
+    if (st == LARGE_FINAL)
+        return;
+    // inverse transform over m1 of the next stage input, twiddle, store Y column m2
+    grp.inverse(x);
+    if (valid) {
+        cx<T>* y = reinterpret_cast<cx<T>*>(A.Y) + e0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int j1 = t + j * P;
+            const cx<T> w = gload<T>(A.twN, ((long long)j1 * m2) & (N - 1));
+            y[j * estride] = cmul(x[j], w);      // * exp(+2 pi i j1 m2 / N)
+        }
+    }
+}
+
+}  // namespace cme

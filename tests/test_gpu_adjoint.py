@@ -66,9 +66,10 @@ def test_segments_do_not_change_the_gradient():
 
 
 def test_grad_matches_central_differences_fp64():
-    """N=256, 400 steps of the sweep-like dynamics; central differences (eps = 1e-6, fourth-order
-    stencil, so that the O(eps^2) truncation of D2, D3 -- which move omega at mu = 128 by
-    8e3 eps -- stays below round-off) of the GPU FP64 loss agree with the adjoint to 1e-6."""
+    """N=256, 400 steps of the sweep-like dynamics; central differences of the GPU FP64 loss
+    agree with the adjoint to 1e-6.  Steps are 1e-6 relative to each parameter's value (D2 =
+    0.01, D3 = 1e-4 move omega at mu = 128 by D mu^2/2, D mu^3/6, so an absolute 1e-6 step in
+    D3 would shift the edge resonances by 0.35) and the stencil is fourth order."""
     N, h, n = 256, 2e-3, 400
     inst = wl.make_instance(N, 0.01, 1e-4, 3.0, 2.0, 1e-3, seed=60)
     T = [target_for(N, 61)]
@@ -81,36 +82,39 @@ def test_grad_matches_central_differences_fp64():
             setattr(i2, k, v)
         return gpu_grad([i2], h, n, T)["loss"][0]
 
-    e = 1e-6
-    checks = [("sigma", lambda s: loss(sigma=inst.sigma + s), g["d_sigma"][0]),
-              ("D2", lambda s: loss(omega=inst.omega + s * mu ** 2 / 2), g["d_D2"][0]),
-              ("D3", lambda s: loss(omega=inst.omega + s * mu ** 3 / 6), g["d_D3"][0]),
-              ("Are", lambda s: loss(A_in=inst.A_in + s), g["d_A_in"][0].real),
-              ("Aim", lambda s: loss(A_in=inst.A_in + 1j * s), g["d_A_in"][0].imag)]
+    checks = [("sigma", 3.0e-6, lambda s: loss(sigma=inst.sigma + s), g["d_sigma"][0]),
+              ("D2", 1e-8, lambda s: loss(omega=inst.omega + s * mu ** 2 / 2), g["d_D2"][0]),
+              ("D3", 1e-10, lambda s: loss(omega=inst.omega + s * mu ** 3 / 6), g["d_D3"][0]),
+              ("Are", 2e-6, lambda s: loss(A_in=inst.A_in + s), g["d_A_in"][0].real),
+              ("Aim", 2e-6, lambda s: loss(A_in=inst.A_in + 1j * s), g["d_A_in"][0].imag)]
     rng = np.random.default_rng(62)
     for r in range(3):
         v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
-        checks.append((f"D0_{r}", lambda s, v=v: loss(D0=inst.D0 + s * v),
+        v *= 1e-3 / np.linalg.norm(v)          # direction of the size of the noise floor
+        checks.append((f"D0_{r}", 1e-6, lambda s, v=v: loss(D0=inst.D0 + s * v),
                        float(np.real(np.vdot(g["d_D0"], v)))))
-    for name, f, ad in checks:
+    for name, e, f, ad in checks:
         fd = (8 * (f(e) - f(-e)) - (f(2 * e) - f(-2 * e))) / (12 * e)
         assert abs(fd - ad) <= 1e-6 * max(abs(fd), abs(ad)), (name, fd, ad)
 
 
 def test_fp32_adjoint_close_to_fp64():
-    """The FP32 adjoint (FP32 cotangents, FP64 parameter accumulators) against the FP64 one:
-    the parameter gradients are cancelling sums over noise-level modes whose log-spectrum
-    cotangents are ~1/|D|, so FP32 keeps about 3 digits (measured 2.8e-3 on d_sigma)."""
+    """The FP32 adjoint (FP32 field and cotangents, FP64 parameter accumulators) against the
+    FP64 one on fields whose modes all sit far above FP32 resolution.  (With noise-level modes
+    -- |D_mu| ~ 1e-6 beside an O(1) pump mode -- the FP32 field itself carries errors of order
+    1e-7 of the comb on those modes, so their log-power terms, and gradients weighted towards
+    them such as dL/dD2, are only loosely determined in FP32; gradient checks use FP64.)"""
     N, h, n = 512, 5e-4, 300
-    insts = wl.sweep512(indices=[40, 200]).instances
+    insts = [wl.random_instance(N, 75 + k, amp=0.3 * np.sqrt(64.0 / N), sigma=1.0 + k,
+                                A_in=1.5, D2=0.02) for k in range(2)]
     T = [target_for(N, 70 + k) for k in range(2)]
     g64 = gpu_grad(insts, h, n, T, cme.FP64)
     g32 = gpu_grad(insts, h, n, T, cme.FP32)
     for key in ("d_sigma", "d_D2", "d_A_in"):
         a, b = np.asarray(g32[key]), np.asarray(g64[key])
-        assert np.max(np.abs(a - b)) <= 1e-2 * np.max(np.abs(b)), key
-    assert np.linalg.norm(g32["d_D0"] - g64["d_D0"]) <= 1e-2 * np.linalg.norm(g64["d_D0"])
-    assert np.max(np.abs(g32["loss"] - g64["loss"])) <= 1e-4 * np.max(np.abs(g64["loss"]))
+        assert np.max(np.abs(a - b)) <= 1e-3 * np.max(np.abs(b)), key
+    assert np.linalg.norm(g32["d_D0"] - g64["d_D0"]) <= 1e-3 * np.linalg.norm(g64["d_D0"])
+    assert np.max(np.abs(g32["loss"] - g64["loss"])) <= 1e-5 * np.max(np.abs(g64["loss"]))
 
 
 def test_torch_autograd_wrapper():

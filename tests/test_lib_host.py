@@ -49,7 +49,7 @@ def test_create_validates_on_host(lib):
     with pytest.raises(cme.CmeError) as e:
         cme.Instance(N, kap, om, 1.0, 0.5, 1.0, 0.0)
     assert e.value.code == -2
-    for bad in (2, 8192, 0, -4):
+    for bad in (2, 1 << 21, 0, -4):
         with pytest.raises(cme.CmeError) as e:
             cme.Instance(bad, np.ones(max(bad, 1)), np.zeros(max(bad, 1)), 1.0, 0.5, 1.0, 0.0)
         assert e.value.code == -2
