@@ -203,6 +203,74 @@ def run_reference(args, world, rank):
     return 0
 
 
+# ------------------------------------------------------------------------------ adjoint
+def run_adjoint(args, world, rank, local):
+    """cme_grad on N=4096 x 16 instances, 10000 RK4IP steps, log-spectrum loss against seeded
+    sech^2 targets: forward with sqrt(n) checkpoints plus the discrete adjoint, FP32; the FP64
+    adjoint is timed on a shorter horizon for comparison."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1307_3428_gb300 import cme
+    from paper_1307_3428_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    w = wl.adjoint4096()
+    nsteps = args.inner_steps or w.nsteps
+    N, B = 4096, len(w.instances)
+    T = wl.sech2_target(N, B).reshape(-1)
+    insts = [cme.Instance.from_workload(i) for i in w.instances]
+    D0 = np.concatenate([i.D0 for i in w.instances])
+    d0 = torch.from_numpy(D0.view(np.float64).copy()).cuda()
+
+    def timed(prec, n, reps):
+        b = cme.Batch(insts, precision=prec)
+        b.set_state_device(d0.data_ptr())
+        b.grad(w.h, n, T)                      # warm-up (allocates the scratch)
+        ts = []
+        for _ in range(reps):
+            b.set_state_device(d0.data_ptr())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = b.grad(w.h, n, T)              # synchronises
+            ts.append(time.perf_counter() - t0)
+        return min(ts), g
+
+    launches0 = cme.kernel_launches()
+    t32, g32 = timed(cme.FP32, nsteps, args.steps)
+    launches = (cme.kernel_launches() - launches0) // (args.steps + 1)
+    n64 = min(nsteps, 1000)
+    t64, g64 = timed(cme.FP64, n64, 1)
+    _, g32s = timed(cme.FP32, n64, 1)
+    mode_steps = N * B * nsteps
+    flops = mode_steps * (34 * 5 * math.log2(N) + 300)
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / t32 / 1e12
+    rel = lambda a, b: float(np.max(np.abs(np.asarray(a) - np.asarray(b))) /
+                             np.max(np.abs(np.asarray(b))))
+    line = {
+        "metric": "gradient mode-steps/s (forward + discrete adjoint), log-spectrum loss",
+        "value": mode_steps / t32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": 1, "ms_per_step": t32 * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"adjoint_n4096_b16: N=4096 x 16, {nsteps} RK4IP steps of "
+                               "h=2e-4, sqrt(n) checkpoints, sech^2 log-spectrum targets"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "basis": "34 transforms of 5 N log2 N + 300 flop per mode-step"},
+        "fp64": {"value": N * B * n64 / t64, "steps": n64},
+        "error": {"fp32_vs_fp64_at_%d_steps" % n64: {
+            "loss": rel(g32s["loss"], g64["loss"]), "d_sigma": rel(g32s["d_sigma"], g64["d_sigma"]),
+            "d_A_in": rel(g32s["d_A_in"], g64["d_A_in"]), "d_D0": rel(g32s["d_D0"], g64["d_D0"])}},
+        "gpu_launches": int(launches),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------------ GPU arm
 def run_gpu(args, world, rank, local):
     import numpy as np
@@ -428,7 +496,7 @@ def main():
     ap.add_argument("--radix", type=int, default=0, help="field values per thread (0: default)")
     ap.add_argument("--inst-per-cta", type=int, default=0, help="instances per block (0: default)")
     ap.add_argument("--workload", default="sweep512",
-                    choices=["sweep512", "uneven", "plain64", "octave"],
+                    choices=["sweep512", "uneven", "plain64", "octave", "adjoint"],
                     help="sweep512 is the headline workload; the others are secondary records")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--autotune", action="store_true")
@@ -442,6 +510,8 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, world, rank)
+        if args.workload == "adjoint":
+            return run_adjoint(args, world, rank, local)
         return run_gpu(args, world, rank, local)
     finally:
         if world > 1:

@@ -279,7 +279,14 @@ struct Transform {
     struct Addr {
         int rd;
         int wr[NS > 1 ? NS - 1 : 1];
+        int wx0, wx1, rx0, rx1;   // XOR-layout bases of the stride-8 exchange (R = 8)
     };
+    // The exchange after a radix-8 pass of stride L = 8 uses the XOR layout
+    // p -> p ^ (8 * bit6(p)) instead of the padding: its writes (p = 64 (t >> 3) + (t & 7) + 8j)
+    // and reads (p = t + jP) then hit 16 distinct 8-byte banks per half-warp, and every address
+    // is one of two per-thread bases plus a compile-time offset.
+    CME_HD static constexpr bool xor8(int s) { return R == 8 && PL::L(s) == 8 && P >= 16; }
+
     CME_DEV static Addr make_addr(int t)
     {
         static_assert(R >= 4, "the padding identity needs R >= 4");
@@ -291,6 +298,13 @@ struct Transform {
             const int k = t & (L - 1);
             a.wr[s] = PL::pad((t - k) * R + k);
         }
+        // stride-8 exchange: write base 64 (t >> 3) + (t & 7), flipped by 8 c, c = bit 3 of t
+        const int c = (t >> 3) & 1;
+        const int wb = 64 * (t >> 3) + (t & 7);
+        a.wx0 = wb + 8 * c;       // even j
+        a.wx1 = wb - 8 * c;       // odd j
+        a.rx0 = t ^ (8 * ((t >> 6) & 1));
+        a.rx1 = a.rx0 ^ 8;        // reads whose jP has bit 6 set
         return a;
     }
 
@@ -299,13 +313,23 @@ struct Transform {
     {
         static_assert(PL::radix(s) == R, "exchanges follow full-radix passes");
         constexpr int L = PL::L(s);
+        if constexpr (xor8(s)) {
 #pragma unroll
-        for (int j = 0; j < R; ++j)
-            b.put(ad.wr[s] + j * L + ((j * L) >> 4), x[j]);
-        group_sync<WARP>();
+            for (int j = 0; j < R; ++j)
+                b.put(((j & 1) ? ad.wx1 : ad.wx0) + 8 * j, x[j]);
+            group_sync<WARP>();
 #pragma unroll
-        for (int j = 0; j < R; ++j)
-            x[j] = b.get(ad.rd + j * P + ((j * P) >> 4));
+            for (int j = 0; j < R; ++j)
+                x[j] = b.get((((j * P) >> 6) & 1 ? ad.rx1 : ad.rx0) + j * P);
+        } else {
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                b.put(ad.wr[s] + j * L + ((j * L) >> 4), x[j]);
+            group_sync<WARP>();
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                x[j] = b.get(ad.rd + j * P + ((j * P) >> 4));
+        }
     }
 
     // buf: the first of two ping-pong buffers (the second starts BUF elements later); par

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
         }
         return;
     }
-    const T gN = (T)(A.g0[inst] / (double)N);
+    const T gN = (T)A.g0[inst] * ((T)1 / (T)N);   // N is a power of two: exact scaling
     grp.rhs(x, gN, cx<T>{T(0), T(0)});   // forward(i g0/N |a|^2 a) over j2, natural m2
     cx<T>* zrow = reinterpret_cast<cx<T>*>(A.Z) + ibase + (long long)j1 * N2 + t;
     if (valid) {
