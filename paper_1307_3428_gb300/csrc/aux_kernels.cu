@@ -78,8 +78,20 @@ __global__ void prop_kernel(PropArgs a)
     }
 }
 
-// centred public index of transform position pm within an instance of size N
-__device__ __forceinline__ int centred_of(int pm, int N) { return (pm + N / 2) & (N - 1); }
+// Centred public index of the mode stored at internal position q of an instance of size N.
+// Up to N = 4096 the internal order is the transform order m = mu mod N; above, the four-step
+// groups store mode m = m1 N2 + m2 column-major at q = m2 N1 + m1 (N1 = 2^ceil(log2 N / 2)),
+// so that their column kernels read the per-mode state contiguously.
+__device__ __forceinline__ int centred_of(int q, int N)
+{
+    int pm = q;
+    if (N > 4096) {
+        const int l = 31 - __clz(N);
+        const int l1 = (l + 1) / 2;
+        pm = ((q & ((1 << l1) - 1)) << (l - l1)) + (q >> l1);
+    }
+    return (pm + N / 2) & (N - 1);
+}
 
 __global__ void import_kernel(int prec, int total, const int* mode_inst, const int* inst_N,
                               const long long* inst_off, const double2* src, void* hi, void* lo)

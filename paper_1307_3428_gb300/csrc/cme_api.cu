@@ -565,8 +565,11 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         const int N = v[i]->N;
         const long long o0 = b->off_h[i];
         const double om0 = v[i]->omega[N / 2];
+        const int l = ilog2i(N), l1 = (l + 1) / 2, l2 = l / 2;
         for (int c = 0; c < N; ++c) {
-            const int pm = (c + N / 2) & (N - 1);  // transform position of centred index c
+            int pm = (c + N / 2) & (N - 1);  // transform position of centred index c
+            if (N > 4096)                    // four-step groups: column-major m2 N1 + m1
+                pm = ((pm & ((1 << l2) - 1)) << l1) + (pm >> l2);
             kap[o0 + pm] = v[i]->kappa[c];
             om[o0 + pm] = v[i]->omega[c] - om0;
             mi[o0 + pm] = i;

@@ -16,8 +16,10 @@
 //   col: load Z column m2, forward over j1, pump, Runge-Kutta combination of the stage (the
 //        same increment form as the in-block kernels), inverse over m1 of the next stage's
 //        input, twiddle, store Y column m2.
-// The field, the accumulator S and the propagators stay in HBM (L2-resident at these sizes);
-// Y and Z are the inter-pass buffers (scratch).
+// The field, the accumulator S and the propagators stay in HBM (L2-resident at these sizes),
+// stored column-major (mode m1 N2 + m2 at position m2 N1 + m1) so that the column kernel reads
+// them contiguously; Y (row-major) and Z (column-major) are the inter-pass buffers (scratch),
+// laid out so that both kernels read contiguously and only their stores are strided.
 #pragma once
 
 #include "cme_step.cuh"
@@ -35,8 +37,8 @@ struct LargeArgs {
     void* hi;                // field (FP32: hi part)
     void* lo;                // FP32 compensation word
     void* S;                 // Runge-Kutta accumulator
-    void* Y;                 // [ninst][N1][N2] column-pass output
-    void* Z;                 // [ninst][N1][N2] row-pass output
+    void* Y;                 // [ninst][N1][N2] column-pass output, row-major (j1 N2 + m2)
+    void* Z;                 // [ninst][N2][N1] row-pass output, column-major (m2 N1 + j1)
     const void* E;
     const void* e1;
     const void* e2;
@@ -91,13 +93,13 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
     }
     const T gN = (T)A.g0[inst] * ((T)1 / (T)N);   // N is a power of two: exact scaling
     grp.rhs(x, gN, cx<T>{T(0), T(0)});   // forward(i g0/N |a|^2 a) over j2, natural m2
-    cx<T>* zrow = reinterpret_cast<cx<T>*>(A.Z) + ibase + (long long)j1 * N2 + t;
+    cx<T>* zcol = reinterpret_cast<cx<T>*>(A.Z) + ibase + (long long)t * N1 + j1;
     if (valid) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const int m2 = t + j * P;
             const cx<T> w = gload<T>(A.twN, ((long long)j1 * m2) & (N - 1));
-            zrow[j * P] = cmulc(x[j], w);        // * exp(-2 pi i j1 m2 / N)
+            zcol[(long long)j * P * N1] = cmulc(x[j], w);   // * exp(-2 pi i j1 m2 / N)
         }
     }
 }
@@ -124,9 +126,9 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     grp.setup(smem, g, threadIdx.x - g * P, A.tw1);
     const int t = grp.t;
     const long long ibase = (long long)inst * N;
-    // element j of this thread: row / mode index m1 = t + jP  ->  offset m1 N2 + m2
-    const long long e0 = ibase + (long long)t * N2 + m2;
-    const long long estride = (long long)P * N2;
+    // element j of this thread: m1 (or j1) = t + jP, stored column-major at m2 N1 + t + jP
+    const long long e0 = ibase + (long long)m2 * N1 + t;
+    const long long estride = P;
     const long long f0 = A.base + e0;   // same element in the field / per-mode arrays
 
     cx<T> x[R];
@@ -218,12 +220,12 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     // inverse transform over m1 of the next stage input, twiddle, store Y column m2
     grp.inverse(x);
     if (valid) {
-        cx<T>* y = reinterpret_cast<cx<T>*>(A.Y) + e0;
+        cx<T>* y = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)t * N2 + m2;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const int j1 = t + j * P;
             const cx<T> w = gload<T>(A.twN, ((long long)j1 * m2) & (N - 1));
-            y[j * estride] = cmul(x[j], w);      // * exp(+2 pi i j1 m2 / N)
+            y[(long long)j * P * N2] = cmul(x[j], w);      // * exp(+2 pi i j1 m2 / N)
         }
     }
 }
