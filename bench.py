@@ -364,7 +364,9 @@ def run_gpu(args, world, rank, local):
         with open(tfile) as fh:
             tj = json.load(fh)
         ent = tj.get("step_kernel_fp32_n512")
-        if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("steps") == nsteps:
+        # the captured kernel must be the one timed here (same sources, same workload shape)
+        if (headline and ent and ent.get("source_hash") == kernel_source_hash()
+                and not args.radix and not args.strang):
             traffic = ent.get("dram_bytes_per_launch")
     if prec_main == cme.FP64:
         peak = FP64_NOMINAL_TFLOPS
