@@ -226,7 +226,7 @@ def run_adjoint(args, world, rank, local):
     d0 = torch.from_numpy(D0.view(np.float64).copy()).cuda()
 
     def timed(prec, n, reps):
-        b = cme.Batch(insts, precision=prec)
+        b = cme.Batch(insts, precision=prec, cluster=args.cluster)
         b.set_state_device(d0.data_ptr())
         b.grad(w.h, n, T)                      # warm-up (allocates the scratch)
         ts = []
@@ -245,7 +245,9 @@ def run_adjoint(args, world, rank, local):
     t64, g64 = timed(cme.FP64, n64, 1)
     _, g32s = timed(cme.FP32, n64, 1)
     mode_steps = N * B * nsteps
-    flops = mode_steps * (34 * 5 * math.log2(N) + 300)
+    # forward, recomputation and backward: three times the forward step's 8 transforms of
+    # 5 N log2 N flop plus ~80 pointwise flop per mode
+    flops = mode_steps * 3 * (8 * 5 * math.log2(N) + 80)
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / t32 / 1e12
     rel = lambda a, b: float(np.max(np.abs(np.asarray(a) - np.asarray(b))) /
@@ -256,10 +258,12 @@ def run_adjoint(args, world, rank, local):
         "warmup": 1, "ms_per_step": t32 * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"adjoint_n4096_b16: N=4096 x 16, {nsteps} RK4IP steps of "
-                               "h=2e-4, sqrt(n) checkpoints, sech^2 log-spectrum targets"},
+                               "h=2e-4, sqrt(n) checkpoints, sech^2 log-spectrum targets",
+                   "cluster": args.cluster or "library choice"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "basis": "34 transforms of 5 N log2 N + 300 flop per mode-step"},
+                     "basis": "3 x (8 transforms of 5 N log2 N + 80) flop per mode-step: forward, "
+                              "checkpoint recomputation, backward"},
         "fp64": {"value": N * B * n64 / t64, "steps": n64},
         "error": {"fp32_vs_fp64_at_%d_steps" % n64: {
             "loss": rel(g32s["loss"], g64["loss"]), "d_sigma": rel(g32s["d_sigma"], g64["d_sigma"]),
@@ -303,6 +307,7 @@ def run_gpu(args, world, rank, local):
     prec_main = cme.FP64 if args.workload == "plain64" else cme.FP32
     b32 = cme.Batch(insts, precision=prec_main, use_graph=True, radix=args.radix,
                     inst_per_cta=args.inst_per_cta, persistent=args.persistent,
+                    cluster=args.cluster,
                     integrator=cme.STRANG if args.strang else cme.RK4IP)
     plan = None
     if args.autotune:
@@ -501,6 +506,8 @@ def main():
                     choices=["sweep512", "uneven", "plain64", "octave", "adjoint"],
                     help="sweep512 is the headline workload; the others are secondary records")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="blocks per instance for N = 2048 / 4096 (0: library choice)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--strang", action="store_true", help="Strang split step instead of RK4IP")
     ap.add_argument("--skip-fp64", action="store_true")

@@ -69,9 +69,19 @@ typedef struct cme_options {
     int inst_per_cta;      /* instances sharing one thread block; 0 = library choice */
     long steps_per_launch; /* steps per kernel launch; 0 = all steps of a call in one launch */
     int use_graph;         /* 1 = cme_step replays a cached CUDA graph per (h, nsteps) */
-    int persistent;        /* batches with several N: 0 = library choice, 1 = one kernel per
-                              N group (concurrent streams), 2 = one persistent work-list
+    int persistent;        /* batches with several N: 0 = library choice (1), 1 = one kernel
+                              per N group (concurrent streams), 2 = one persistent work-list
                               kernel for all groups */
+    int cluster;           /* thread blocks per instance (1, 2, 4 or 8) for N = 2048 and 4096
+                              at 8 values per thread: C > 1 spreads each instance over a
+                              thread-block cluster whose blocks exchange through distributed
+                              shared memory (one kernel per N group; also used by cme_grad).
+                              0 = library choice: FP64 batches take the largest C with
+                              instances * C <= SMs (FP64 arithmetic is the bound, so more
+                              SMs per instance pay); FP32 batches take C = 1 (their exchanges
+                              are latency bound, and a cluster exchange costs more than an
+                              in-block one).  Groups without a compiled cluster shape run
+                              C = 1. */
 } cme_options;
 
 /* Fill *opt with the defaults: CME_FP64, CME_RK4IP, library-chosen launch shape, no graph. */
@@ -178,9 +188,11 @@ typedef struct cme_grads {
 /* Run nsteps RK4IP steps from the current field with checkpoints every `segment` steps (0 =
  * ceil(sqrt(nsteps))), evaluate L against the target T (total_modes doubles: log10 powers,
  * centred, host memory), then run the discrete adjoint backwards, recomputing each segment from
- * its checkpoint.  The batch ends at the final field (tau advanced by h nsteps).  Scratch
- * memory (checkpoints, one segment of states, stage values) is allocated on the first call and
- * kept with the batch.  RK4IP batches only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM. */
+ * its checkpoint (the recomputation of the next segment overlaps the backward pass of the
+ * current one, on a second stream).  The batch ends at the final field (tau advanced by
+ * h nsteps).  Scratch memory -- ceil(nsteps/segment) checkpoints and the states plus stage
+ * values of two segments, 8 * segment field vectors -- is allocated on the first call and kept
+ * with the batch.  RK4IP batches only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM. */
 int cme_grad(cme_batch b, double h, long nsteps, const double* target, double eps, long segment,
              cme_grads* out);
 

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("integrator", ctypes.c_int),
                 ("radix", ctypes.c_int), ("inst_per_cta", ctypes.c_int),
                 ("steps_per_launch", ctypes.c_long), ("use_graph", ctypes.c_int),
-                ("persistent", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("cluster", ctypes.c_int)]
 
 
 class Grads(ctypes.Structure):
@@ -190,7 +190,7 @@ class Batch:
 
     def __init__(self, instances: Sequence, precision=FP64, integrator=RK4IP, radix=0,
                  inst_per_cta=0, steps_per_launch=0, use_graph=False, stream=None,
-                 persistent=0):
+                 persistent=0, cluster=0):
         lib = load()
         insts = [i if isinstance(i, Instance) else Instance.from_workload(i) for i in instances]
         opt = Options()
@@ -199,6 +199,7 @@ class Batch:
         opt.radix, opt.inst_per_cta = int(radix), int(inst_per_cta)
         opt.steps_per_launch, opt.use_graph = int(steps_per_launch), int(bool(use_graph))
         opt.persistent = int(persistent)
+        opt.cluster = int(cluster)
         arr = (ctypes.c_void_p * len(insts))(*[i.handle.value for i in insts])
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(stream) if stream else None

@@ -8,9 +8,15 @@
 //     bbar = IDFT(-i g0 ybar) / N,   abar = 2 |a|^2 bbar + a^2 conj(bbar),   xbar = DFT(abar),
 // evaluated with the same transform code as the forward pass.
 //
-// Memory: the forward pass stores the field at the start of every segment of K steps
-// (checkpoints); the backward kernel recomputes one segment at a time from its checkpoint
-// into a segment buffer, then walks it backwards.
+// Memory and schedule: the forward pass stores the field at the start of every segment of K
+// steps (checkpoints).  The backward pass then walks the segments in reverse.  For each segment
+// s, a recompute kernel regenerates, from its checkpoint, the state D, the stage values
+// y1 = F(D), k2, k3 and the time-domain fields a = IDFT(stage input) of the four stages of
+// every step into one half of a two-segment buffer.  A backward kernel then runs the four
+// vector-Jacobian products of every step of s from that half (two transforms each, since a
+// comes from the buffer).  The
+// recomputation of segment s - 1 does not depend on any cotangent, so the host runs it on a
+// second stream while segment s runs backwards: only the products are on the critical path.
 #pragma once
 
 #include "cme_adjoint_args.h"
@@ -21,184 +27,248 @@ namespace cme {
 template <typename T>
 CME_DEV cx<T> cconj(cx<T> a) { return {a.re, -a.im}; }
 
-template <typename T, int LOGN, int R>
-__global__ void __launch_bounds__(max_threads<LOGN, R>()) adjoint_kernel(const AdjArgs A)
+// Accumulator of one mode's L cotangent over the steps of a segment; the running total lives in
+// FP64 in memory between segments.  FP64 kernels continue the total term by term (so the sum,
+// and the gradient, do not depend on the segment length).  FP32 kernels keep the segment's
+// terms in a compensated float pair (exact two-sum per term) and add it to the total once per
+// segment: FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU, and a convert-and-add
+// per term made it the bottleneck of the backward pass.
+template <typename T>
+struct LAcc;
+template <>
+struct LAcc<double> {
+    double2 v;
+    CME_DEV void init(double2 total) { v = total; }
+    CME_DEV void add(cx<double> d)
+    {
+        v.x += d.re;
+        v.y += d.im;
+    }
+    CME_DEV double2 finish(double2) const { return v; }
+};
+template <>
+struct LAcc<float> {
+    float hr, hi, lr, li;
+    CME_DEV void init(double2) { hr = hi = lr = li = 0.f; }
+    CME_DEV static void two_sum(float& h, float& l, float d)
+    {
+        const float s = h + d, b = s - h;
+        l += (h - (s - b)) + (d - b);
+        h = s;
+    }
+    CME_DEV void add(cx<float> d)
+    {
+        two_sum(hr, lr, d.re);
+        two_sum(hi, li, d.im);
+    }
+    CME_DEV double2 finish(double2 total) const
+    {
+        return make_double2(total.x + ((double)hr + (double)lr), total.y + ((double)hi + (double)li));
+    }
+};
+
+// Per-instance set-up shared by both roles.  C > 1: each instance is spread over a cluster of
+// C blocks (grid = ninst * C blocks of P/C threads, cluster dimension C).
+template <typename T, int LOGN, int R, int C>
+CME_DEV int adj_setup(Group<T, LOGN, R, C>& grp, unsigned char* smem, const StepArgs& a,
+                      bool& valid)
 {
-    using GR = Group<T, LOGN, R>;
+    constexpr int P = Group<T, LOGN, R, C>::P;
+    int inst;
+    valid = true;
+    if constexpr (C == 1) {
+        const int g = threadIdx.x / P;
+        inst = blockIdx.x * a.G + g;
+        valid = inst < a.ninst;
+        if (!valid)
+            inst = a.ninst - 1;
+        grp.setup(smem, g, threadIdx.x - g * P, a.tw);
+    } else {
+        inst = blockIdx.x / C;
+        grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw);
+    }
+    return inst;
+}
+
+template <int LOGN, int R, int C>
+constexpr int adj_threads() { return C == 1 ? max_threads<LOGN, R>() : Plan<LOGN, R>::P / C; }
+
+// Recompute role: the states of segment A.seg from its checkpoint, and the stage values
+// y1, k2, k3 of every step, into half (A.seg mod 2) of A.stages.
+template <typename T, int LOGN, int R, int C = 1>
+__global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(const AdjArgs A)
+{
+    using GR = Group<T, LOGN, R, C>;
     constexpr int N = GR::N, P = GR::P;
     extern __shared__ __align__(16) unsigned char smem[];
     const StepArgs& a = A.s;
-
-    const int g = threadIdx.x / P;
-    int inst = blockIdx.x * a.G + g;
-    const bool valid = inst < a.ninst;
-    if (!valid)
-        inst = a.ninst - 1;
     GR grp;
-    grp.setup(smem, g, threadIdx.x - g * P, a.tw);
+    bool valid;
+    const int inst = adj_setup(grp, smem, a, valid);
     const int t = grp.t;
     const long long off = a.base + (long long)inst * N;
-
-    FieldState<T, LOGN, R> fs;
+    FieldState<T, LOGN, R, C> fs;
     fs.bind(grp);
     const StepConsts<T> c = step_consts<T>(a, inst, N);
-    Props<T, LOGN, R> pr;
+    Props<T, LOGN, R, C> pr;
+    pr.init(a, off, t);
+    const long long TT = A.total, s = A.seg;
+    const long long ns = (A.nsteps - s * A.K < A.K) ? A.nsteps - s * A.K : A.K;
+    fs.load(reinterpret_cast<const cx<T>*>(A.ckpt_hi) + s * TT + off + t,
+            reinterpret_cast<const cx<T>*>(A.ckpt_lo) + s * TT + off + t);
+    // this thread's slots of step 0 of the segment (surplus groups of a packed block recompute
+    // the last instance for the barriers and store nothing)
+    cx<T>* out = reinterpret_cast<cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + t;
+    if constexpr (C > 1)
+        cluster_sync();   // every block of the cluster runs before the first remote store
+    for (long long i = 0; i < ns; ++i) {
+        cx<T>* o = out + i * ADJ_VECS * TT;
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                o[j * P] = fs.Dh[j];
+        }
+        rk4ip_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
+    }
+    if constexpr (C > 1)
+        cluster_sync();   // no block leaves while a peer may still address its shared memory
+}
+
+// Backward role: the discrete adjoint of the steps of segment A.seg, last step first, from
+// the states and stage values in half (A.seg mod 2) of A.stages.  The field cotangent, the
+// L cotangents and the pump cotangent are carried between segments in A.dbar, A.gL, A.pbar.
+template <typename T, int LOGN, int R, int C = 1>
+__global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(const AdjArgs A)
+{
+    using GR = Group<T, LOGN, R, C>;
+    constexpr int N = GR::N, P = GR::P;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const StepArgs& a = A.s;
+    GR grp;
+    bool valid;
+    const int inst = adj_setup(grp, smem, a, valid);
+    const int t = grp.t;
+    const long long off = a.base + (long long)inst * N;
+    const StepConsts<T> c = step_consts<T>(a, inst, N);
+    Props<T, LOGN, R, C> pr;
     pr.init(a, off, t);
 
-    cx<T>* seg = reinterpret_cast<cx<T>*>(A.seg) + off + t;
-    cx<T>* yb = reinterpret_cast<cx<T>*>(A.ybuf) + off + t;
+    const long long TT = A.total, s = A.seg;
+    const long long ns = (A.nsteps - s * A.K < A.K) ? A.nsteps - s * A.K : A.K;
+    const cx<T>* buf =
+        reinterpret_cast<const cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + t;
     cx<T>* dbp = reinterpret_cast<cx<T>*>(A.dbar) + off + t;
-    const long long TT = A.total;
+    double2* glp = A.gL + off + t;
 
     cx<T> Db[R];
-    double2 gl[R];
+    LAcc<T> gl[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         Db[j] = dbp[j * P];
-        gl[j] = make_double2(0.0, 0.0);
+        gl[j].init(glp[j * P]);
     }
     double2 pb = make_double2(0.0, 0.0);
+    if (t == 0)
+        pb = A.pbar[inst];
     const T hh = c.hh, h = c.h, h6 = c.h6, h3 = T(2) * c.h6;
     const T gNn = c.gN;  // g0 / N
+    if constexpr (C > 1)
+        cluster_sync();   // every block of the cluster runs before the first remote store
 
-    for (long long s = A.S - 1; s >= 0; --s) {
-        const long long n0 = s * A.K;
-        const long long ns = (A.nsteps - n0 < A.K) ? A.nsteps - n0 : A.K;
-        // recompute the segment's states from its checkpoint
-        fs.load(reinterpret_cast<const cx<T>*>(A.ckpt_hi) + s * TT + off + t,
-                reinterpret_cast<const cx<T>*>(A.ckpt_lo) + s * TT + off + t);
-        for (long long i = 0; i < ns; ++i) {
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                seg[i * TT + j * P] = fs.Dh[j];
-            if (i + 1 < ns)
-                rk4ip_step(grp, fs, pr, c);
-        }
-        // walk the segment backwards
-        for (long long i = ns - 1; i >= 0; --i) {
-            const cx<T>* Dn = seg + i * TT;
-            // forward stage values of step i: y1 = F(D), k2 = F(x2), k3 = F(x3)
-            cx<T> x[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                x[j] = Dn[j * P];
+    for (long long i = ns - 1; i >= 0; --i) {
+        // step i: D, then y1, k2, k3, then a of the stage inputs D, x2, x3, x4, at TT strides
+        const cx<T>* Dn = buf + i * ADJ_VECS * TT;
+        const cx<T>* yb = Dn + TT;
+        const cx<T>* ab = Dn + 4 * TT;
+        // reverse stages 3 (x4), 2 (x3), 1 (x2), 0 (D)
+        cx<T> ub[R], cot[R];
 #pragma unroll 1
-            for (int st = 0; st < 3; ++st) {
-                grp.rhs(x, c.gN, c.pump);
+        for (int st = 3; st >= 0; --st) {
+            cx<T> z[R];
+            if (st == 3) {
+                // cotangent of k4 = F(x4), and the E-cotangent from D' = E w + h/6 k4:
+                // conj(hh E) conj(w) Dbar', w = u + h/6 (E y1 + 2 (k2 + k3))
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    yb[st * TT + j * P] = x[j];
                     const cx<T> E = pr.getE(j);
                     const cx<T> u = cmul(E, Dn[j * P]);
-                    if (st == 0)
-                        x[j] = caxpy(u, hh, cmul(E, x[j]));        // x2 = u + h/2 E y1
-                    else if (st == 1)
-                        x[j] = caxpy(u, hh, x[j]);                  // x3 = u + h/2 k2
+                    const cx<T> y1 = yb[j * P], k2 = yb[TT + j * P], k3 = yb[2 * TT + j * P];
+                    cot[j] = cscale(Db[j], h6);
+                    const cx<T> w = caxpy(u, h6, cadd(cmul(E, y1), cscale(cadd(k2, k3), T(2))));
+                    gl[j].add(cmulc(cmulc(Db[j], w), cscale(E, hh)));
                 }
             }
-            // reverse stages 3 (x4), 2 (x3), 1 (x2), 0 (D)
-            cx<T> ub[R], cot[R];
+            if (t == 0) {
+                pb.x += (double)cot[0].re;
+                pb.y += (double)cot[0].im;
+            }
+            // zbar = J_F(z)^H cot, a = IDFT(stage input) from the buffer: bbar =
+            // IDFT(-i (g0/N) cot), then DFT(2 |a|^2 bbar + a^2 conj(bbar)) (two transforms
+            // through one call site)
+            const cx<T>* as = ab + st * TT;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                z[j] = {gNn * cot[j].im, -gNn * cot[j].re};
 #pragma unroll 1
-            for (int st = 3; st >= 0; --st) {
-                cx<T> z[R];
-                // stage input and the cotangent of its F output
+            for (int p = 0; p < 2; ++p) {
+                if (p == 1) {
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const cx<T> E = pr.getE(j);
+                    for (int j = 0; j < R; ++j) {
+                        const cx<T> a = as[j * P];
+                        const cx<T> bb = z[j];                   // bbar
+                        const T p2 = a.re * a.re + a.im * a.im;
+                        const cx<T> a2 = cmul(a, a);
+                        const cx<T> abar = caxpy(cmulc(a2, bb), T(2) * p2, bb);
+                        z[j] = cconj(abar);                      // DFT(.) = conj(IDFT(conj .))
+                    }
+                }
+                grp.inverse(z);
+            }
+            // z now holds conj(stage-input cotangent)
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cx<T> xb = cconj(z[j]);
+                if (st == 0) {
+                    Db[j] = cadd(Db[j], xb);
+                    continue;
+                }
+                const cx<T> E = pr.getE(j);
+                const cx<T> wb = cmulc(Db[j], E);                // conj(E) Dbar'
+                const cx<T> hE = cscale(E, hh);
+                if (st == 3) {
+                    const cx<T> u = cmul(E, Dn[j * P]);
+                    const cx<T> v = caxpy(u, h, yb[2 * TT + j * P]);
+                    const cx<T> vb = cmulc(xb, E);               // conj(E) x4bar
+                    gl[j].add(cmulc(cmulc(xb, v), hE));          // conj(hh E) conj(v) x4bar
+                    ub[j] = cadd(wb, vb);
+                    cot[j] = caxpy(cscale(wb, h3), h, vb);       // k3bar
+                } else if (st == 2) {
+                    ub[j] = cadd(ub[j], xb);
+                    cot[j] = caxpy(cscale(wb, h3), hh, xb);      // k2bar
+                } else {   // st == 1
+                    ub[j] = cadd(ub[j], xb);
+                    const cx<T> k1b = caxpy(cscale(wb, h6), hh, xb);
+                    const cx<T> y1 = yb[j * P];
                     const cx<T> D = Dn[j * P];
-                    const cx<T> u = cmul(E, D);
-                    if (st == 3) {
-                        const cx<T> y1 = yb[j * P], k2 = yb[TT + j * P], k3 = yb[2 * TT + j * P];
-                        const cx<T> v = caxpy(u, h, k3);
-                        z[j] = cmul(E, v);                           // x4 = E (u + h k3)
-                        cot[j] = cscale(Db[j], h6);                  // k4bar
-                        // E-cotangent from D' = E w + ...: conj(w) Dbar'
-                        const cx<T> w = caxpy(u, h6, cadd(cmul(E, y1), cscale(cadd(k2, k3), T(2))));
-                        const cx<T> lb = cmulc(cmulc(Db[j], w), cscale(E, hh));   // conj(hh E) conj(w) Db
-                        gl[j].x += (double)lb.re;
-                        gl[j].y += (double)lb.im;
-                    } else if (st == 2) {
-                        z[j] = caxpy(u, hh, yb[TT + j * P]);         // x3
-                    } else if (st == 1) {
-                        z[j] = caxpy(u, hh, cmul(E, yb[j * P]));     // x2
-                    } else {
-                        z[j] = D;
-                    }
-                }
-                if (t == 0) {
-                    pb.x += (double)cot[0].re;
-                    pb.y += (double)cot[0].im;
-                }
-                // zbar = J_F(z)^H cot  (three transforms through one call site)
-                cx<T> aa[R];
-#pragma unroll 1
-                for (int p = 0; p < 3; ++p) {
-                    if (p == 1) {
-#pragma unroll
-                        for (int j = 0; j < R; ++j) {
-                            aa[j] = z[j];                            // a = IDFT(stage input)
-                            // -i (g0/N) cot
-                            z[j] = {gNn * cot[j].im, -gNn * cot[j].re};
-                        }
-                    } else if (p == 2) {
-#pragma unroll
-                        for (int j = 0; j < R; ++j) {
-                            const cx<T> bb = z[j];                   // bbar
-                            const T p2 = aa[j].re * aa[j].re + aa[j].im * aa[j].im;
-                            const cx<T> a2 = cmul(aa[j], aa[j]);
-                            const cx<T> ab = caxpy(cmulc(a2, bb), T(2) * p2, bb);
-                            z[j] = cconj(ab);                        // DFT(ab) = conj(IDFT(conj ab))
-                        }
-                    }
-                    grp.inverse(z);
-                }
-                // z now holds conj(stage-input cotangent)
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const cx<T> xb = cconj(z[j]);
-                    const cx<T> E = pr.getE(j);
-                    const cx<T> D = Dn[j * P];
-                    const cx<T> u = cmul(E, D);
-                    const cx<T> wb = cmulc(Db[j], E);                // conj(E) Dbar'
-                    const cx<T> hE = cscale(E, hh);
-                    if (st == 3) {
-                        const cx<T> v = caxpy(u, h, yb[2 * TT + j * P]);
-                        const cx<T> vb = cmulc(xb, E);               // conj(E) x4bar
-                        const cx<T> lb = cmulc(cmulc(xb, v), hE);    // conj(hh E) conj(v) x4bar
-                        gl[j].x += (double)lb.re;
-                        gl[j].y += (double)lb.im;
-                        ub[j] = cadd(wb, vb);
-                        cot[j] = caxpy(cscale(wb, h3), h, vb);       // k3bar
-                    } else if (st == 2) {
-                        ub[j] = cadd(ub[j], xb);
-                        cot[j] = caxpy(cscale(wb, h3), hh, xb);      // k2bar
-                    } else if (st == 1) {
-                        ub[j] = cadd(ub[j], xb);
-                        const cx<T> k1b = caxpy(cscale(wb, h6), hh, xb);
-                        const cx<T> y1 = yb[j * P];
-                        const cx<T> l1 = cmulc(cmulc(ub[j], D), hE);  // conj(hh E) conj(D) ubar
-                        const cx<T> l2 = cmulc(cmulc(k1b, y1), hE);   // conj(hh E) conj(y1) k1bar
-                        gl[j].x += (double)l1.re + (double)l2.re;
-                        gl[j].y += (double)l1.im + (double)l2.im;
-                        Db[j] = cmulc(ub[j], E);                     // conj(E) ubar
-                        cot[j] = cmulc(k1b, E);                      // y1bar = conj(E) k1bar
-                    } else {
-                        Db[j] = cadd(Db[j], xb);
-                    }
+                    gl[j].add(cmulc(cmulc(ub[j], D), hE));       // conj(hh E) conj(D) ubar
+                    gl[j].add(cmulc(cmulc(k1b, y1), hE));        // conj(hh E) conj(y1) k1bar
+                    Db[j] = cmulc(ub[j], E);                     // conj(E) ubar
+                    cot[j] = cmulc(k1b, E);                      // y1bar = conj(E) k1bar
                 }
             }
         }
     }
     if (valid) {
-        double2* glp = A.gL + off + t;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             dbp[j * P] = Db[j];
-            glp[j * P] = gl[j];
+            glp[j * P] = gl[j].finish(glp[j * P]);
         }
         if (t == 0)
             A.pbar[inst] = pb;
     }
+    if constexpr (C > 1)
+        cluster_sync();   // no block leaves while a peer may still address its shared memory
 }
 
 }  // namespace cme

@@ -10,14 +10,21 @@ struct AdjArgs {
     long long nsteps;        // steps of the forward run
     long long K;             // steps per segment
     long long S;             // segments
+    long long seg;           // the segment this launch handles
     long long total;         // modes in the batch (stride of the per-segment arrays)
     const void* ckpt_hi;     // [S][total] field at the segment starts (transform order)
     const void* ckpt_lo;     // [S][total] compensation words (FP32)
-    void* seg;               // [K][total] hi part of the states of the current segment
-    void* ybuf;              // [3][total] y1 = F(D), k2, k3 of the step being reversed
-    void* dbar;              // [total] in: cotangent of the final field; out: of the initial
+    void* stages;            // [2][K][ADJ_VECS][total]: per step of a segment, D, y1 = F(D),
+                             // k2, k3, then a = IDFT(stage input) of D, x2, x3, x4; segment s
+                             // uses half s mod 2
+    void* dbar;              // [total] cotangent of the field (carried between launches)
     double2* gL;             // [total] accumulated cotangent of L_mu (re: dL/dRe L, im: dL/dIm L)
     double2* pbar;           // [ninst] cotangent of the pump sqrt(kappa_ext) A_in
 };
+
+// Kernel roles of one segment: recompute the states and stage values, or run it backwards.
+enum { ADJ_BACKWARD = 0, ADJ_RECOMPUTE = 1 };
+// Field vectors stored per step of a segment.
+constexpr int ADJ_VECS = 8;
 
 }  // namespace cme

@@ -117,7 +117,10 @@ bool shape_compiled(int logN, int R)
     return false;
 }
 
-int default_radix(int logN) { return logN <= 2 ? 4 : 8; }
+// Values per thread: 8, except N = 4096 in FP32, where 16 values per thread (256 threads, up to
+// 255 registers) beat 8 (512 threads, at most 128 registers, spilling): 19.3 against 22.8 us
+// per step measured on GB300.
+int default_radix(int logN, int prec) { return logN <= 2 ? 4 : (logN == 12 && prec == PREC_FP32 ? 16 : 8); }
 
 }  // namespace
 
@@ -133,6 +136,7 @@ struct LaunchGroup {
     int first = 0, count = 0;   // instances [first, first+count)
     long long base = 0;         // first mode offset
     int R = 8, G = 1;
+    int C = 1;                  // blocks per instance (thread-block cluster when > 1)
     // N > 4096: four-step split N = N1 N2 (column length N1, row length N2)
     bool large = false;
     int logN1 = 0, logN2 = 0, G1 = 1, G2 = 1;
@@ -186,8 +190,9 @@ struct cme_batch_s {
 
     // gradient scratch (allocated by the first cme_grad call, grown when needed)
     long long g_S = 0, g_K = 0;
-    void *g_ckpt_hi = nullptr, *g_ckpt_lo = nullptr, *g_seg = nullptr, *g_ybuf = nullptr,
-         *g_dbar = nullptr;
+    void *g_ckpt_hi = nullptr, *g_ckpt_lo = nullptr, *g_stages = nullptr, *g_dbar = nullptr;
+    cudaStream_t g_side = nullptr;              // recomputation stream of cme_grad
+    cudaEvent_t g_ev[4] = {};                   // fork, recomputed, backward done (x2)
     double2 *g_gL = nullptr, *g_pbar = nullptr, *g_dD0 = nullptr;
     double *g_loss = nullptr, *g_red = nullptr, *g_target = nullptr, *g_domega = nullptr,
            *g_dkappa = nullptr;
@@ -227,12 +232,32 @@ struct cme_batch_s {
 
 namespace {
 
+// Instances per block of a per-group kernel with R values per thread (G = 0: library choice).
+int inst_per_block(int N, int R, int G, int count)
+{
+    const int P = N / R;
+    if (G == 0)
+        G = P >= 64 ? 1 : std::max(1, 64 / P);
+    G = std::min(G, std::max(1, 256 / P));
+    if (P >= 64)
+        return 1;   // kernels for groups of >= 64 threads are compiled for one instance per block
+    if (P < 32) {
+        // groups narrower than a warp synchronise with __syncwarp over full warps: make the
+        // block a whole number of warps (surplus groups recompute the last instance and store
+        // nothing)
+        const int per_warp = 32 / P;
+        return std::max(per_warp, (G + per_warp - 1) / per_warp * per_warp);
+    }
+    return std::min(G, count);
+}
+
 // (Re)compute the launch plan of every group from the options: values per thread R and
 // instances per block G of the per-group kernels, and the persistent work-list tiles.
 int plan_batch(cme_batch b, const cme_options& o)
 {
     if (o.steps_per_launch < 0 || o.inst_per_cta < 0 || o.radix < 0 || o.persistent < 0 ||
-        o.persistent > 2)
+        o.persistent > 2 || !(o.cluster == 0 || o.cluster == 1 || o.cluster == 2 ||
+                              o.cluster == 4 || o.cluster == 8))
         return fail(CME_ERR_INVALID_ARG, "launch plan: invalid option");
     bool any_large = false;
     for (auto& g : b->groups) {
@@ -247,33 +272,35 @@ int plan_batch(cme_batch b, const cme_options& o)
             any_large = true;
             continue;
         }
-        int R = o.radix ? o.radix : default_radix(g.logN);
+        int R = o.radix ? o.radix : default_radix(g.logN, b->prec);
         if (R > g.N)
             R = g.N;
         if (!shape_compiled(g.logN, R))
             return fail(CME_ERR_INVALID_ARG, "launch plan: radix %d not available for N=%d", R, g.N);
         g.R = R;
-        const int P = g.N / R;
-        int G = o.inst_per_cta;
-        if (G == 0)
-            G = P >= 64 ? 1 : std::max(1, 64 / P);
-        G = std::min(G, std::max(1, 256 / P));
-        if (P >= 64) {
-            G = 1;  // kernels for groups of >= 64 threads are compiled for one instance per block
-        } else if (P < 32) {
-            // groups narrower than a warp synchronise with __syncwarp over full warps: make the
-            // block a whole number of warps (surplus groups recompute the last instance and
-            // store nothing)
-            const int per_warp = 32 / P;
-            G = std::max(per_warp, (G + per_warp - 1) / per_warp * per_warp);
-        } else {
-            G = std::min(G, g.count);
+        g.G = inst_per_block(g.N, R, o.inst_per_cta, g.count);
+        // blocks per instance: explicit, or (FP64 only) the largest cluster that still gives
+        // every instance's blocks their own SMs.  FP64 groups are bound by the FP64 pipes, so
+        // spreading an instance over C SMs pays (N = 4096 x 16: 437 -> 136 us per step); FP32
+        // groups are latency bound and each distributed-shared-memory exchange costs ~0.7 us,
+        // so they run one block per instance unless asked otherwise.
+        g.C = 1;
+        if (o.cluster > 1) {
+            if (cluster_shape_compiled(g.logN, R, o.cluster))
+                g.C = o.cluster;
+        } else if (o.cluster == 0 && b->prec == PREC_FP64 && (g.logN == 11 || g.logN == 12)) {
+            for (int c : {8, 4, 2})
+                if (cluster_shape_compiled(g.logN, R, c) && (long long)g.count * c <= b->sms) {
+                    g.C = c;
+                    break;
+                }
         }
-        g.G = G;
     }
+    // library choice: one kernel per N group on concurrent streams (measured ahead of the
+    // work-list kernel on the uneven N = 256 ... 4096 workload: 1.13 s against 1.22 s)
     int mode = o.persistent;
     if (mode == 0)
-        mode = b->groups.size() > 1 ? 2 : 1;
+        mode = 1;
     if (any_large)
         mode = 1;   // four-step groups run their own kernel sequence
     if (mode == 2) {
@@ -304,6 +331,7 @@ int plan_batch(cme_batch b, const cme_options& o)
     b->opt.steps_per_launch = o.steps_per_launch;
     b->opt.use_graph = o.use_graph;
     b->opt.persistent = mode;
+    b->opt.cluster = o.cluster;
     b->clear_graphs();
     return CME_OK;
 }
@@ -390,6 +418,11 @@ void cme_batch_destroy(cme_batch b)
     b->clear_graphs();
     for (void* p : b->g_allocs)
         dev_free(p, b->free_fn, b->free_ctx);
+    for (cudaEvent_t e : b->g_ev)
+        if (e)
+            cudaEventDestroy(e);
+    if (b->g_side)
+        cudaStreamDestroy(b->g_side);
     for (cudaStream_t st : b->side)
         cudaStreamDestroy(st);
     for (cudaEvent_t e : b->ev)
@@ -491,12 +524,14 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
             }
             continue;
         }
-        const int R = std::min(o.radix ? o.radix : default_radix(g.logN), g.N);
-        if (!shape_compiled(g.logN, R) || o.persistent < 0 || o.persistent > 2) {
+        const int R = std::min(o.radix ? o.radix : default_radix(g.logN, b->prec), g.N);
+        if (!shape_compiled(g.logN, R) || o.persistent < 0 || o.persistent > 2 ||
+            !(o.cluster == 0 || o.cluster == 1 || o.cluster == 2 || o.cluster == 4 ||
+              o.cluster == 8)) {
             cme_batch_destroy(b);
             return fail(CME_ERR_INVALID_ARG,
-                        "cme_batch_create: launch option (radix %d, persistent %d) not available "
-                        "for N=%d", R, o.persistent, g.N);
+                        "cme_batch_create: launch option (radix %d, persistent %d, cluster %d) "
+                        "not available for N=%d", R, o.persistent, o.cluster, g.N);
         }
     }
     if (cuda_stream) {
@@ -703,6 +738,9 @@ cudaError_t launch_group_step(cme_batch b, LaunchGroup& g, long long nsteps, cud
     StepArgs a = group_args(b, g);
     a.nsteps = nsteps;
     ++g_launches;
+    if (g.C > 1)
+        return b->prec == PREC_FP64 ? launch_cluster_step_fp64(b->method, g.logN, g.R, g.C, a, st)
+                                    : launch_cluster_step_fp32(b->method, g.logN, g.R, g.C, a, st);
     if (b->prec == PREC_FP64)
         return b->method == METHOD_RK4IP ? launch_step_fp64_rk4ip(g.logN, g.R, a, st)
                                          : launch_step_fp64_strang(g.logN, g.R, a, st);
@@ -999,7 +1037,8 @@ std::string tune_key(cme_batch b, double h)
     return k;
 }
 
-// Optional persistence: CME_TUNE_CACHE names a text file of "key<TAB>radix G persistent" lines.
+// Optional persistence: CME_TUNE_CACHE names a text file of
+// "key<TAB>radix G persistent cluster" lines.
 void tune_cache_load()
 {
     if (g_tune_loaded)
@@ -1019,7 +1058,8 @@ void tune_cache_load()
         *tab = 0;
         cme_options o;
         cme_default_options(&o);
-        if (sscanf(tab + 1, "%d %d %d", &o.radix, &o.inst_per_cta, &o.persistent) == 3)
+        if (sscanf(tab + 1, "%d %d %d %d", &o.radix, &o.inst_per_cta, &o.persistent,
+                   &o.cluster) == 4)
             g_tune_cache[line] = o;
     }
     fclose(f);
@@ -1034,7 +1074,8 @@ void tune_cache_store(const std::string& key, const cme_options& o)
     FILE* f = fopen(path, "a");
     if (!f)
         return;
-    fprintf(f, "%s\t%d %d %d\n", key.c_str(), o.radix, o.inst_per_cta, o.persistent);
+    fprintf(f, "%s\t%d %d %d %d\n", key.c_str(), o.radix, o.inst_per_cta, o.persistent,
+            o.cluster);
     fclose(f);
 }
 
@@ -1059,6 +1100,7 @@ int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out)
             o.radix = it->second.radix;
             o.inst_per_cta = it->second.inst_per_cta;
             o.persistent = it->second.persistent;
+            o.cluster = it->second.cluster;
             int rc = plan_batch(b, o);
             if (rc == CME_OK) {
                 if (plan_out)
@@ -1084,6 +1126,17 @@ int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out)
                 o.radix = R;
                 o.inst_per_cta = G;
                 o.persistent = 1;
+                o.cluster = 1;
+                cand.push_back(o);
+            }
+            for (int C : {2, 4, 8}) {
+                if (!cluster_shape_compiled(g.logN, R, C))
+                    continue;
+                cme_options o = base;
+                o.radix = R;
+                o.inst_per_cta = 0;
+                o.persistent = 1;
+                o.cluster = C;
                 cand.push_back(o);
             }
         }
@@ -1093,11 +1146,14 @@ int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out)
         o.persistent = 2;
         cand.push_back(o);
     } else {
-        for (int pers : {2, 1}) {
+        // the work-list kernel, then per-group kernels with each cluster size (the cluster
+        // size applies to the groups that have a cluster shape)
+        for (int C : {0, 1, 2, 4, 8}) {
             cme_options o = base;
             o.radix = 0;
             o.inst_per_cta = 0;
-            o.persistent = pers;
+            o.persistent = C == 0 ? 2 : 1;
+            o.cluster = C == 0 ? 0 : C;
             cand.push_back(o);
         }
     }
@@ -1419,8 +1475,7 @@ int ensure_grad_scratch(cme_batch b, long long S, long long K)
     };
     b->g_ckpt_hi = A(S * T * E);
     b->g_ckpt_lo = b->prec == PREC_FP32 ? A(S * T * E) : nullptr;
-    b->g_seg = A(K * T * E);
-    b->g_ybuf = A(3 * T * E);
+    b->g_stages = A(2 * K * ADJ_VECS * T * E);
     b->g_dbar = A(T * E);
     b->g_gL = (double2*)A(T * 16);
     b->g_pbar = (double2*)A(C * 16);
@@ -1437,6 +1492,14 @@ int ensure_grad_scratch(cme_batch b, long long S, long long K)
         b->g_S = b->g_K = 0;
         return fail(CME_ERR_OOM, "cme_grad: cannot allocate %lld checkpoints x %lld modes", S,
                     (long long)T);
+    }
+    if (!b->g_side) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->g_side, cudaStreamNonBlocking);
+        for (auto& ev : b->g_ev)
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cme_grad: recomputation stream");
     }
     b->g_S = S;
     b->g_K = K;
@@ -1483,26 +1546,61 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
     CME_CUDA(launch_loss_seed(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, b->hi,
                               b->lo, b->g_target, eps, b->g_loss, b->g_dbar, st),
              "cme_grad: seed");
-    // backward, one launch per group
-    for (auto& g : b->groups) {
-        AdjArgs A{};
-        A.s = group_args(b, g);
-        A.nsteps = nsteps;
-        A.K = K;
-        A.S = S;
-        A.total = b->total;
-        A.ckpt_hi = b->g_ckpt_hi;
-        A.ckpt_lo = b->g_ckpt_lo ? b->g_ckpt_lo : b->g_ckpt_hi;
-        A.seg = b->g_seg;
-        A.ybuf = b->g_ybuf;
-        A.dbar = b->g_dbar;
-        A.gL = b->g_gL;
-        A.pbar = b->g_pbar + g.first;
-        ++g_launches;
-        cudaError_t e = b->prec == PREC_FP64 ? launch_adjoint_fp64(g.logN, g.R, A, st)
-                                             : launch_adjoint_fp32(g.logN, g.R, A, st);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "cme_grad: adjoint kernel");
+    // backward: segments in reverse.  The recomputation of segment s (states and stage values,
+    // independent of every cotangent) runs on the side stream into half s mod 2 of the stage
+    // buffer while segment s + 1 runs backwards on the batch stream from the other half.
+    CME_CUDA(cudaMemsetAsync(b->g_gL, 0, (size_t)b->total * 16, st), "cme_grad: zero");
+    CME_CUDA(cudaMemsetAsync(b->g_pbar, 0, (size_t)b->count * 16, st), "cme_grad: zero");
+    auto run_segment = [&](int role, long long sg, cudaStream_t str) -> cudaError_t {
+        for (auto& g : b->groups) {
+            // The adjoint kernels address the field by mode position, so they need not share
+            // the forward plan's values per thread: they take 8 (their live state is larger
+            // than a forward step's; at N = 4096 FP32, 8 values per thread without spills beat
+            // 16: 66.5 against 74.4 us per gradient step).  Cluster groups keep their plan.
+            LaunchGroup ga = g;
+            if (g.C == 1) {
+                ga.R = std::min(default_radix(g.logN, PREC_FP64), g.N);
+                ga.G = inst_per_block(g.N, ga.R, 0, g.count);
+            }
+            AdjArgs A{};
+            A.s = group_args(b, ga);
+            A.nsteps = nsteps;
+            A.K = K;
+            A.S = S;
+            A.seg = sg;
+            A.total = b->total;
+            A.ckpt_hi = b->g_ckpt_hi;
+            A.ckpt_lo = b->g_ckpt_lo ? b->g_ckpt_lo : b->g_ckpt_hi;
+            A.stages = b->g_stages;
+            A.dbar = b->g_dbar;
+            A.gL = b->g_gL;
+            A.pbar = b->g_pbar + g.first;
+            ++g_launches;
+            cudaError_t e = b->prec == PREC_FP64
+                                ? launch_adjoint_fp64(role, ga.logN, ga.R, ga.C, A, str)
+                                : launch_adjoint_fp32(role, ga.logN, ga.R, ga.C, A, str);
+            if (e != cudaSuccess)
+                return e;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t ev_fork = b->g_ev[0], ev_rec = b->g_ev[1], ev_back[2] = {b->g_ev[2], b->g_ev[3]};
+    cudaStream_t side = b->g_side;
+    CME_CUDA(cudaEventRecord(ev_fork, st), "cme_grad: fork");
+    CME_CUDA(cudaStreamWaitEvent(side, ev_fork, 0), "cme_grad: fork");
+    CME_CUDA(run_segment(ADJ_RECOMPUTE, S - 1, side), "cme_grad: recompute");
+    CME_CUDA(cudaEventRecord(ev_rec, side), "cme_grad: recompute");
+    for (long long sg = S - 1; sg >= 0; --sg) {
+        CME_CUDA(cudaStreamWaitEvent(st, ev_rec, 0), "cme_grad: join");
+        CME_CUDA(run_segment(ADJ_BACKWARD, sg, st), "cme_grad: adjoint kernel");
+        CME_CUDA(cudaEventRecord(ev_back[sg & 1], st), "cme_grad: backward");
+        if (sg >= 1) {
+            // half (sg - 1) mod 2 was last read by the backward pass of segment sg + 1
+            if (sg + 1 <= S - 1)
+                CME_CUDA(cudaStreamWaitEvent(side, ev_back[(sg + 1) & 1], 0), "cme_grad: wait");
+            CME_CUDA(run_segment(ADJ_RECOMPUTE, sg - 1, side), "cme_grad: recompute");
+            CME_CUDA(cudaEventRecord(ev_rec, side), "cme_grad: recompute");
+        }
     }
     g_launches += 2;
     CME_CUDA(launch_grad_reduce(b->count, b->inst_N, b->inst_off, b->g_gL, b->g_loss, b->g_red, st),

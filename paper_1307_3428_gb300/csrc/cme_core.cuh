@@ -199,6 +199,39 @@ CME_DEV void dft(cx<T> (&v)[r])
 }
 
 // ----------------------------------------------------------------------------------------
+// Thread-block clusters: one instance spread over C blocks of a cluster, exchanging through
+// distributed shared memory (stores into the peer block's shared memory, then a cluster
+// barrier whose release/acquire makes them visible).
+// ----------------------------------------------------------------------------------------
+CME_DEV uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// address of the same shared-memory offset in block `rank` of this cluster
+CME_DEV uint32_t dsmem_map(uint32_t a, int rank)
+{
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+CME_DEV void dsmem_put(uint32_t a, float re, float im)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(re), "f"(im) : "memory");
+}
+CME_DEV void dsmem_put(uint32_t a, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+CME_DEV void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+CME_DEV int cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+
+// ----------------------------------------------------------------------------------------
 // Shared-memory exchange buffer: float2 words for FP32, separate re/im arrays for FP64 (so
 // both are 8-byte accesses with the same bank pattern).
 // ----------------------------------------------------------------------------------------
@@ -213,6 +246,8 @@ struct Xbuf<float> {
         return {a.x, a.y};
     }
     CME_DEV Xbuf at(int off) const { return {p + off}; }
+    // element at DSMEM address a (a maps element i of some block's buffer)
+    CME_DEV void put_remote(uint32_t a, cx<float> v) const { dsmem_put(a, v.re, v.im); }
     static constexpr int words_per_elem = 1;  // in 8-byte words
 };
 template <>
@@ -226,6 +261,11 @@ struct Xbuf<double> {
     }
     CME_DEV cx<double> get(int i) const { return {re[i], re[i + stride]}; }
     CME_DEV Xbuf at(int off) const { return {re + 2 * off, stride}; }
+    CME_DEV void put_remote(uint32_t a, cx<double> v) const
+    {
+        dsmem_put(a, v.re);
+        dsmem_put(a + 8u * (uint32_t)stride, v.im);
+    }
     static constexpr int words_per_elem = 2;
 };
 
@@ -238,14 +278,25 @@ CME_DEV void group_sync()
         __syncthreads();
 }
 
+
 // ----------------------------------------------------------------------------------------
 // Transform of one group: x holds positions t + j*P; sign S (+1 inverse / time samples,
 // -1 forward).  tw holds exp(+2 pi i j k/(L r)) for the passes s >= 1.
+//
+// C > 1: the group's P threads are spread over the C blocks of a thread-block cluster, PC =
+// P/C threads each (thread t = rank PC + l).  Each block's exchange buffer holds the N/C
+// positions its own threads read, position t + jP at local index l + j PC (padded); a pass
+// stores each output straight into the buffer of the block that reads it next.
 // ----------------------------------------------------------------------------------------
-template <typename T, int LOGN, int R, bool WARP>
+template <typename T, int LOGN, int R, bool WARP, int C = 1>
 struct Transform {
     using PL = Plan<LOGN, R>;
     static constexpr int N = PL::N, P = PL::P, NS = PL::NS;
+    static_assert(C >= 1 && (C & (C - 1)) == 0 && P % C == 0, "cluster size");
+    static constexpr int PC = P / C;                 // threads per block of the cluster
+    static_assert(C == 1 || PC % 16 == 0, "padding identity needs PC % 16 == 0");
+    // elements per exchange buffer of one block
+    static constexpr int BUFC = C == 1 ? PL::BUF : N / C + N / C / 16 + 1;
 
     template <int s, int S, class TW>
     CME_DEV static void pass(cx<T> (&x)[R], const TW& tw)
@@ -280,6 +331,8 @@ struct Transform {
         int rd;
         int wr[NS > 1 ? NS - 1 : 1];
         int wx0, wx1, rx0, rx1;   // XOR-layout bases of the stride-8 exchange (R = 8)
+        // C > 1: DSMEM address of every store of every exchange (buffer 0)
+        uint32_t wc[C > 1 && NS > 1 ? NS - 1 : 1][C > 1 ? R : 1];
     };
     // The exchange after a radix-8 pass of stride L = 8 uses the XOR layout
     // p -> p ^ (8 * bit6(p)) instead of the padding: its writes (p = 64 (t >> 3) + (t & 7) + 8j)
@@ -308,27 +361,66 @@ struct Transform {
         return a;
     }
 
+    // C > 1: thread t = rank PC + l; buf_saddr = shared address of this block's buffer 0.
+    // The store of output j of pass s goes to position p = (t - k) R + k + jL (k = t mod L),
+    // which is read by thread p mod P, i.e. by block (p mod P) / PC at local index
+    // (p mod PC) + (p / P) PC.
+    CME_DEV static Addr make_addr_cluster(int t, int l, uint32_t buf_saddr)
+    {
+        Addr a{};
+        a.rd = PL::pad(l);
+        if constexpr (C > 1) {
+#pragma unroll
+            for (int s = 0; s + 1 < NS; ++s) {
+                const int L = PL::L(s);
+                const int k = t & (L - 1);
+                const int b = (t - k) * R + k;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const int p = b + j * L;
+                    const int q = p & (P - 1);
+                    const int loc = (q & (PC - 1)) + (p / P) * PC;
+                    a.wc[s][j] = dsmem_map(buf_saddr + 8u * (uint32_t)PL::pad(loc), q / PC);
+                }
+            }
+        }
+        return a;
+    }
+
     template <int s>
-    CME_DEV static void exchange(cx<T> (&x)[R], const Xbuf<T>& b, const Addr& ad)
+    CME_DEV static void exchange(cx<T> (&x)[R], const Xbuf<T>& b, const Addr& ad, int par)
     {
         static_assert(PL::radix(s) == R, "exchanges follow full-radix passes");
         constexpr int L = PL::L(s);
-        if constexpr (xor8(s)) {
+        if constexpr (C > 1) {
+            // buffer `par` of the reading block: par * BUFC elements of W 8-byte words further
+            const uint32_t po = (uint32_t)par * (uint32_t)(BUFC * 8 * Xbuf<T>::words_per_elem);
+            const Xbuf<T> mine = b.at(par * BUFC);
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                b.put(((j & 1) ? ad.wx1 : ad.wx0) + 8 * j, x[j]);
+                mine.put_remote(ad.wc[s][j] + po, x[j]);
+            cluster_sync();
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                x[j] = mine.get(ad.rd + j * PC + ((j * PC) >> 4));
+        } else if constexpr (xor8(s)) {
+            const Xbuf<T> mine = b.at(par * BUFC);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                mine.put(((j & 1) ? ad.wx1 : ad.wx0) + 8 * j, x[j]);
             group_sync<WARP>();
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                x[j] = b.get((((j * P) >> 6) & 1 ? ad.rx1 : ad.rx0) + j * P);
+                x[j] = mine.get((((j * P) >> 6) & 1 ? ad.rx1 : ad.rx0) + j * P);
         } else {
+            const Xbuf<T> mine = b.at(par * BUFC);
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                b.put(ad.wr[s] + j * L + ((j * L) >> 4), x[j]);
+                mine.put(ad.wr[s] + j * L + ((j * L) >> 4), x[j]);
             group_sync<WARP>();
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                x[j] = b.get(ad.rd + j * P + ((j * P) >> 4));
+                x[j] = mine.get(ad.rd + j * P + ((j * P) >> 4));
         }
     }
 
@@ -340,7 +432,7 @@ struct Transform {
     {
         pass<s, S>(x, tw);
         if constexpr (s + 1 < NS) {
-            exchange<s>(x, buf.at(par * PL::BUF), ad);
+            exchange<s>(x, buf, ad, par);
             par ^= 1;
             run_from<s + 1, S, TW>(x, tw, buf, par, ad);
         }

@@ -47,6 +47,18 @@ __host__ __device__ constexpr size_t group_smem_bytes(int tbytes, int logN, int 
                                          : 0);
 }
 
+// Cluster launches: one instance spread over the C blocks of a thread-block cluster.  Compiled
+// for R = 8 with (log2 N, C) in {(8, 2)} (small case for tests) and {11, 12} x {2, 4, 8}.
+__host__ __device__ constexpr bool cluster_shape_compiled(int logN, int R, int C)
+{
+    return R == 8 && ((logN == 8 && C == 2) || ((logN == 11 || logN == 12) &&
+                                                (C == 2 || C == 4 || C == 8)));
+}
+cudaError_t launch_cluster_step_fp32(int method, int logN, int R, int C, const StepArgs& a,
+                                     cudaStream_t s);
+cudaError_t launch_cluster_step_fp64(int method, int logN, int R, int C, const StepArgs& a,
+                                     cudaStream_t s);
+
 // Launch one uniform-N group; implemented per precision and method in the kernel units.
 cudaError_t launch_step_fp64_rk4ip(int logN, int R, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp64_strang(int logN, int R, const StepArgs& a, cudaStream_t s);
@@ -111,8 +123,15 @@ cudaError_t launch_grad_export(int prec, int total, const int* mode_inst, const 
                                const double* red, double2* dD0, double* domega, double* dkappa,
                                cudaStream_t s);
 struct AdjArgs;  // cme_adjoint_args.h
-cudaError_t launch_adjoint_fp32(int logN, int R, const AdjArgs& a, cudaStream_t s);
-cudaError_t launch_adjoint_fp64(int logN, int R, const AdjArgs& a, cudaStream_t s);
+// C = blocks per instance (1: instances packed a.s.G per block; 2, 4, 8: thread-block cluster
+// per instance, for the shapes cluster_shape_compiled accepts).
+// role = ADJ_BACKWARD or ADJ_RECOMPUTE (cme_adjoint_args.h), for segment a.seg.
+cudaError_t launch_adjoint_fp32(int role, int logN, int R, int C, const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_fp64(int role, int logN, int R, int C, const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_cluster_fp32(int role, int logN, int R, int C, const AdjArgs& a,
+                                        cudaStream_t s);
+cudaError_t launch_adjoint_cluster_fp64(int role, int logN, int R, int C, const AdjArgs& a,
+                                        cudaStream_t s);
 
 }  // namespace cme
 

@@ -20,6 +20,12 @@ namespace cme {
     X(11, 8) X(11, 16)                 \
     X(12, 8) X(12, 16)
 
+// Cluster shapes (log2 N, R, C); must agree with cluster_shape_compiled.
+#define CME_FOR_EACH_CLUSTER_SHAPE(X) \
+    X(8, 8, 2)                         \
+    X(11, 8, 2) X(11, 8, 4) X(11, 8, 8) \
+    X(12, 8, 2) X(12, 8, 4) X(12, 8, 8)
+
 template <typename T>
 inline size_t smem_bytes_for(int logN, int R, int G)
 {
@@ -32,6 +38,37 @@ inline cudaError_t prepare_smem(KernelT k, size_t smem)
     if (smem > 48 * 1024)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaSuccess;
+}
+
+// Launch `blocks` blocks of `threads` threads in clusters of C blocks along x.
+template <typename KernelT, typename ArgT>
+inline cudaError_t launch_clustered(KernelT k, int blocks, int threads, size_t smem, int C,
+                                    cudaStream_t s, const ArgT& a)
+{
+    cudaError_t e = prepare_smem(k, smem);
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
+template <typename T, int LOGN, int R, int C, int METHOD>
+inline cudaError_t launch_cluster_step_shape(const StepArgs& a, cudaStream_t s)
+{
+    static_assert(cluster_shape_compiled(LOGN, R, C), "cluster shape list");
+    return launch_clustered(cluster_step_kernel<T, LOGN, R, C, METHOD>, a.ninst * C,
+                            Plan<LOGN, R>::P / C, cluster_smem_bytes<T, LOGN, R, C>(), C, s, a);
 }
 
 template <typename T, int LOGN, int R, int METHOD>

@@ -15,9 +15,10 @@ constexpr int max_threads() { return Plan<LOGN, R>::P >= 64 ? Plan<LOGN, R>::P :
 // Per-mode propagators of the RK4IP and Strang steps: E = exp(L h/2), e1 = expm1(L h/2),
 // e2 = expm1(L h).  For FP32 groups up to N = 1024 they are held in registers for the whole
 // launch; otherwise they are read through the read-only cache where used.
-template <typename T, int LOGN, int R>
+template <typename T, int LOGN, int R, int C = 1>
 struct Props {
-    static constexpr bool IN_REGS = sizeof(T) == 4 && LOGN <= 10 && R <= 8;
+    // cluster groups run few threads per block, so their register budget has room
+    static constexpr bool IN_REGS = sizeof(T) == 4 && (LOGN <= 10 || C > 1) && R <= 8;
     cx<T> E[IN_REGS ? R : 1], e1[IN_REGS ? R : 1], e2[IN_REGS ? R : 1];
     const cx<T>* pE;   // pointers pre-offset to (instance offset + t)
     const cx<T>* pe1;
@@ -66,13 +67,14 @@ template <typename T, int LOGN>
 constexpr bool twiddles_in_regs() { return sizeof(T) == 4 ? LOGN <= 10 : LOGN <= 9; }
 
 // Per-thread view of one instance: the transform machinery plus the instance constants.
-template <typename T, int LOGN, int R>
+// C > 1: the instance is spread over the C blocks of a thread-block cluster.
+template <typename T, int LOGN, int R, int C = 1>
 struct Group {
     using PL = Plan<LOGN, R>;
     static constexpr int N = PL::N, P = PL::P;
-    static constexpr bool WARP = (P <= 32);
+    static constexpr bool WARP = (C == 1 && P <= 32);
     static constexpr bool COMP = (sizeof(T) == 4);  // compensated state in FP32
-    using TF = Transform<T, LOGN, R, WARP>;
+    using TF = Transform<T, LOGN, R, WARP, C>;
     using TW = Twiddles<T, LOGN, R, twiddles_in_regs<T, LOGN>()>;
 
     int t;
@@ -86,11 +88,19 @@ struct Group {
     CME_DEV void inverse(cx<T> (&x)[R]) { TF::template run<+1>(x, tw, buf, par, ad); }
 
     // F(x) = pump + i (g0/N) DFT(|a|^2 a), a = inverse transform of x   (Eq. 4)
-    CME_DEV void rhs(cx<T> (&x)[R], T gN, cx<T> pump)
+    CME_DEV void rhs(cx<T> (&x)[R], T gN, cx<T> pump) { rhs_store_a(x, gN, pump, nullptr); }
+
+    // The same, also storing the time-domain field a at aout[j P] unless aout is null.
+    CME_DEV void rhs_store_a(cx<T> (&x)[R], T gN, cx<T> pump, cx<T>* aout)
     {
 #pragma unroll 1
         for (int d = 0; d < 2; ++d) {
             inverse(x);
+            if (d == 0 && aout) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    aout[j * P] = x[j];
+            }
             if (d == 0) {
                 // conj(i c a) with c = (g0/N) |a|^2
 #pragma unroll
@@ -107,7 +117,7 @@ struct Group {
             x[0] = cadd(x[0], pump);
     }
 
-    static constexpr bool ACC_SMEM = acc_in_smem(sizeof(T), LOGN, R);
+    static constexpr bool ACC_SMEM = C == 1 && acc_in_smem(sizeof(T), LOGN, R);
     cx<T>* accS;   // shared-memory accumulator S (ACC_SMEM), pre-offset by t
     cx<T>* accL;   // shared-memory compensation word (ACC_SMEM, FP32), pre-offset by t
 
@@ -131,7 +141,33 @@ struct Group {
         ad = TF::make_addr(t);
         tw.init(tw_table, t);
     }
+
+    // Cluster set-up (C > 1): block `rank` of the cluster, thread l of the block; the block's
+    // dynamic shared memory holds its two exchange buffers.
+    CME_DEV void setup_cluster(unsigned char* smem, int rank, int l, const void* tw_table)
+    {
+        static_assert(C > 1, "cluster groups only");
+        if constexpr (sizeof(T) == 4) {
+            buf.p = reinterpret_cast<float2*>(smem);
+        } else {
+            buf.re = reinterpret_cast<double*>(smem);
+            buf.stride = TF::BUFC;
+        }
+        accS = nullptr;
+        accL = nullptr;
+        t = rank * TF::PC + l;
+        par = 0;
+        ad = TF::make_addr_cluster(t, l, smem_addr(smem));
+        tw.init(tw_table, t);
+    }
 };
+
+// Dynamic shared memory of one block of a cluster group: two exchange buffers.
+template <typename T, int LOGN, int R, int C>
+constexpr size_t cluster_smem_bytes()
+{
+    return (size_t)2 * Transform<T, LOGN, R, false, C>::BUFC * 8 * Xbuf<T>::words_per_elem;
+}
 
 template <typename T>
 struct Coef;  // step coefficients in the field precision, converted once on the host
@@ -153,9 +189,9 @@ struct Coef<double> {
 // The evolving field of one thread: hi part in registers; the compensation word Dl (FP32) and
 // the Runge-Kutta accumulator S in registers, or (ACC_SMEM) in this thread's own shared-memory
 // slots t + jP.
-template <typename T, int LOGN, int R>
+template <typename T, int LOGN, int R, int C = 1>
 struct FieldState {
-    using GR = Group<T, LOGN, R>;
+    using GR = Group<T, LOGN, R, C>;
     static constexpr int P = GR::P;
     static constexpr bool COMP = GR::COMP, AS = GR::ACC_SMEM;
     cx<T> Dh[R];
@@ -243,18 +279,34 @@ struct StepConsts {
 //   D' = D + e2 D + h/6 [E (k1 + 2 k2 + 2 k3) + k4],  k1 = E F(D),  k_i = F(x_i),
 // with E = exp(L h/2), e1 = expm1(L h/2), e2 = expm1(L h).  The four stages share one copy of
 // the right-hand-side code (a runtime loop).
-template <typename T, int LOGN, int R>
-CME_DEV void rk4ip_step(Group<T, LOGN, R>& grp, FieldState<T, LOGN, R>& fs,
-                        const Props<T, LOGN, R>& pr, const StepConsts<T>& c)
+// STAGES = true also stores, unless so is null (the adjoint's recomputation), the right-hand-side
+// values y1 = F(D), k2 = F(x2), k3 = F(x3) of the thread's positions at so[st * sstride + j P],
+// st = 0, 1, 2, and the time-domain fields a of the four stage inputs D, x2, x3, x4 at
+// so[(3 + st) * sstride + j P], st = 0..3.
+template <bool STAGES, typename T, int LOGN, int R, int C>
+CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                             const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c, cx<T>* so,
+                             long long sstride)
 {
-    constexpr bool COMP = Group<T, LOGN, R>::COMP;
+    constexpr bool COMP = Group<T, LOGN, R, C>::COMP;
+    constexpr int P = Group<T, LOGN, R, C>::P;
     cx<T> x[R];
 #pragma unroll
     for (int j = 0; j < R; ++j)
         x[j] = fs.Dh[j];
 #pragma unroll 1
     for (int st = 0; st < 4; ++st) {
-        grp.rhs(x, c.gN, c.pump);
+        if constexpr (STAGES)
+            grp.rhs_store_a(x, c.gN, c.pump, so ? so + (3 + st) * sstride : nullptr);
+        else
+            grp.rhs(x, c.gN, c.pump);
+        if constexpr (STAGES) {
+            if (st < 3 && so) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    so[st * sstride + j * P] = x[j];
+            }
+        }
         if (st == 0) {
 #pragma unroll
             for (int j = 0; j < R; ++j) {
@@ -290,15 +342,22 @@ CME_DEV void rk4ip_step(Group<T, LOGN, R>& grp, FieldState<T, LOGN, R>& fs,
     }
 }
 
+template <typename T, int LOGN, int R, int C>
+CME_DEV void rk4ip_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                        const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c)
+{
+    rk4ip_step_impl<false>(grp, fs, pr, c, static_cast<cx<T>*>(nullptr), 0);
+}
+
 // One Strang split step (Sec. 2 "split-step Fourier method ... field in the frequency domain"):
 // exact linear+pump flow over h/2, exact Kerr flow over h, exact linear+pump flow over h/2.
 // With a = inverse transform of D the Kerr flow is a -> a exp(i g0 |a|^2 h); it is applied as
 // the increment D += DFT(a expm1(i g0 |a|^2 h))/N.
-template <typename T, int LOGN, int R>
-CME_DEV void strang_step(Group<T, LOGN, R>& grp, FieldState<T, LOGN, R>& fs,
-                         const Props<T, LOGN, R>& pr, const StepConsts<T>& c)
+template <typename T, int LOGN, int R, int C>
+CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                         const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c)
 {
-    constexpr bool COMP = Group<T, LOGN, R>::COMP;
+    constexpr bool COMP = Group<T, LOGN, R, C>::COMP;
     constexpr T invN = (T)(1.0 / (1 << LOGN));
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
@@ -411,6 +470,48 @@ __global__ void __launch_bounds__(max_threads<LOGN, R>()) step_kernel(const Step
 {
     extern __shared__ __align__(16) unsigned char smem[];
     step_body<T, LOGN, R, METHOD>(a, blockIdx.x * a.G, smem);
+}
+
+// The same steps with each instance spread over a cluster of C blocks (P/C threads each);
+// launched with a grid of exactly ninst * C blocks and cluster dimension C, so every block
+// holds a real instance and all of them take part in every cluster barrier.
+template <typename T, int LOGN, int R, int C, int METHOD>
+__global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(const StepArgs a)
+{
+    using GR = Group<T, LOGN, R, C>;
+    constexpr int N = GR::N;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int inst = blockIdx.x / C;
+    GR grp;
+    grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw);
+    const int t = grp.t;
+    const long long off = a.base + (long long)inst * N;
+
+    cx<T>* hi = reinterpret_cast<cx<T>*>(a.hi) + off + t;
+    cx<T>* lo = reinterpret_cast<cx<T>*>(a.lo) + off + t;
+    FieldState<T, LOGN, R, C> fs;
+    fs.bind(grp);
+    fs.load(hi, lo);
+    const StepConsts<T> c = step_consts<T>(a, inst, N);
+    Props<T, LOGN, R, C> pr;
+    pr.init(a, off, t);
+    cluster_sync();   // every block of the cluster runs before the first remote store
+
+    for (long long n = 0; n < a.nsteps; ++n) {
+        if constexpr (METHOD == METHOD_RK4IP)
+            rk4ip_step(grp, fs, pr, c);
+        else
+            strang_step(grp, fs, pr, c);
+    }
+
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        bad |= !(isfinite(fs.Dh[j].re) && isfinite(fs.Dh[j].im));
+    fs.store(hi, lo);
+    if (bad)
+        a.status[inst] = 1;
+    cluster_sync();   // no block leaves while a peer may still address its shared memory
 }
 
 // Diagnostics: one transform or one right-hand-side evaluation of the current field, written in

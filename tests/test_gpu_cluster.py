@@ -1,0 +1,162 @@
+"""Instances spread over a thread-block cluster (cme_options.cluster = C > 1): the C blocks hold
+P/C threads each and exchange through distributed shared memory.
+
+The cluster kernels do the same arithmetic as the one-block kernels, in the same order; only
+where a value waits between two passes differs.  So besides the oracle comparisons (N = 256
+with C = 2 against the direct-sum oracle, N = 2048 and 4096 against the oracle's Eq. 4 engine,
+the adjoint at N = 256 against the oracle's adjoint), the cluster results equal the one-block
+results bit for bit wherever both hold the propagators the same way: always in FP64, and in
+FP32 up to N = 1024.  FP32 cluster kernels for N >= 2048 keep the propagators in registers
+(their blocks are small enough) where the one-block kernel reads them from memory; the
+compiler may then fuse a multiply-add differently, so there the two agree to FP32 rounding."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fft_engine
+from paper_1307_3428_gb300 import cme
+from paper_1307_3428_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    cme.load()
+
+
+def rel(x, y):
+    return float(np.linalg.norm(np.asarray(x) - np.asarray(y)) / np.linalg.norm(np.asarray(y)))
+
+
+def batch_of(insts, prec, integ=cme.RK4IP, **kw):
+    return cme.Batch([cme.Instance.from_workload(i) for i in insts], precision=prec,
+                     integrator=integ, **kw)
+
+
+def same_policies(N, prec):
+    return prec == cme.FP64 or N <= 1024
+
+
+def random_set(N, seed, count):
+    amp = 0.3 * min(1.0, np.sqrt(64.0 / N))
+    return [wl.random_instance(N, seed + k, amp=amp, sigma=0.5 * k, A_in=1.0 + 0.2j * k)
+            for k in range(count)]
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_cluster_n256_rk4ip_matches_direct_sum(prec):
+    insts = random_set(256, 3000, 3)
+    b = batch_of(insts, prec, cluster=2)
+    b.step(1e-3, 6)
+    got = b.split(b.get_state())
+    for g, inst in zip(got, insts):
+        ref = oracle.integrate(inst, 1e-3, 6, oracle.RK4IP)
+        assert rel(g, ref) <= (1e-12 if prec == cme.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_cluster_n256_strang_matches_direct_sum(prec):
+    insts = random_set(256, 3100, 3)
+    b = batch_of(insts, prec, cme.STRANG, cluster=2)
+    b.step(2e-3, 10)
+    got = b.split(b.get_state())
+    for g, inst in zip(got, insts):
+        ref = oracle.integrate(inst, 2e-3, 10, oracle.STRANG)
+        assert rel(g, ref) <= (1e-11 if prec == cme.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N,C", [(2048, 2), (2048, 8), (4096, 4), (4096, 8)])
+def test_cluster_rk4ip_matches_eq4_engine(N, C, prec):
+    insts = random_set(N, 3200 + N, 3)
+    b = batch_of(insts, prec, cluster=C)
+    b.step(1e-3, 20)
+    got = b.split(b.get_state())
+    refs = fft_engine.rk4ip(fft_engine.Batch(insts), 1e-3, 20)
+    for g, r in zip(got, refs):
+        assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("integ", [cme.RK4IP, cme.STRANG])
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N,C", [(256, 2), (2048, 4), (4096, 2), (4096, 8)])
+def test_cluster_equals_one_block_bitwise(N, C, prec, integ):
+    insts = random_set(N, 3300 + N, 3)
+    out = {}
+    for c in (1, C):
+        b = batch_of(insts, prec, integ, cluster=c)
+        b.step(1e-3, 37)
+        b.synchronize()
+        out[c] = b.get_state()
+        b.close()
+    if same_policies(N, prec):
+        assert np.array_equal(out[1], out[C])
+    else:
+        assert rel(out[C], out[1]) <= 1e-6
+
+
+def test_cluster_inside_a_mixed_batch():
+    """N = 4096 instances on clusters next to N = 512 and N = 64 groups, one kernel per group on
+    concurrent streams, against the Eq. 4 engine."""
+    insts = random_set(64, 3400, 2) + random_set(512, 3410, 3) + random_set(4096, 3420, 2)
+    b = batch_of(insts, cme.FP32, persistent=1, cluster=4, use_graph=True)
+    b.step(1e-3, 10)
+    b.step(1e-3, 10)
+    got = b.split(b.get_state())
+    for N in (64, 512, 4096):
+        sel = [k for k, i in enumerate(insts) if i.N == N]
+        refs = fft_engine.rk4ip(fft_engine.Batch([insts[k] for k in sel]), 1e-3, 20)
+        for k, r in zip(sel, refs):
+            assert rel(got[k], r) <= 1e-5, (N, k)
+
+
+def target_for(N, seed):
+    rng = np.random.default_rng(seed)
+    return np.log10(rng.uniform(1e-4, 0.5, N))
+
+
+def test_cluster_adjoint_n256_matches_oracle_adjoint():
+    N, h, n = 256, 0.01, 4
+    insts = [wl.make_instance(N, 0.05, 0.01, 1.3, 1.4 + 0.2j, 0.05, seed=3500 + k)
+             for k in range(2)]
+    T = [target_for(N, 3510 + k) for k in range(2)]
+    b = batch_of(insts, cme.FP64, cluster=2)
+    g = b.grad(h, n, np.concatenate(T))
+    for k, (inst, t) in enumerate(zip(insts, T)):
+        o = oracle.log_spectrum_grad(inst, h, n, t)
+        sl = slice(k * N, (k + 1) * N)
+        assert abs(g["loss"][k] - o["loss"]) <= 1e-11 * abs(o["loss"])
+        assert abs(g["d_sigma"][k] - o["sigma"]) <= 1e-9 * max(abs(o["sigma"]), 1e-6 * abs(o["loss"]))
+        assert abs(g["d_A_in"][k] - o["A_in"]) <= 1e-9 * abs(o["A_in"])
+        assert np.max(np.abs(g["d_D0"][sl] - o["D0"])) <= 1e-9 * np.max(np.abs(o["D0"]))
+        assert np.max(np.abs(g["d_omega"][sl] - o["omega"])) <= 1e-9 * np.max(np.abs(o["omega"]))
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N,C", [(256, 2), (4096, 8)])
+def test_cluster_adjoint_equals_one_block_bitwise(N, C, prec):
+    """Where the policies differ (FP32, N = 4096) the comparison is against the FP64 gradient:
+    parameter gradients are sums over modes that cancel, which FP32 determines only loosely
+    (tenths of a percent here), so the cluster FP32 gradient must be as close to FP64 as the
+    one-block FP32 gradient is."""
+    insts = [wl.make_instance(N, 0.01, 1e-4, 2.0 + k, 2.0, 1e-3, seed=3600 + k) for k in range(2)]
+    T = np.concatenate([target_for(N, 3610 + k) for k in range(2)])
+
+    def grad(p, c):
+        b = batch_of(insts, p, cluster=c)
+        g = b.grad(2e-4, 40, T, segment=7)
+        b.close()
+        return g
+
+    out = {c: grad(prec, c) for c in (1, C)}
+    if same_policies(N, prec):
+        for key in out[1]:
+            assert np.array_equal(out[1][key], out[C][key]), key
+    else:
+        ref = grad(cme.FP64, C)
+        for key in out[1]:
+            e1, eC = rel(out[1][key], ref[key]), rel(out[C][key], ref[key])
+            assert eC <= max(2 * e1, 1e-6), (key, e1, eC)

@@ -79,6 +79,10 @@ def test_batch_create_rejects_bad_arguments(lib):
     with pytest.raises(cme.CmeError) as e:
         cme.Batch([a], radix=2)      # launch shape not compiled
     assert e.value.code == -1
+    for c in (3, 16, -1):            # blocks per instance must be 0, 1, 2, 4 or 8
+        with pytest.raises(cme.CmeError) as e:
+            cme.Batch([a], cluster=c)
+        assert e.value.code == -1 and b"cluster" in lib.cme_last_error()
     out = ctypes.c_void_p()
     assert lib.cme_batch_create(None, 0, None, None, ctypes.byref(out)) == -1
     assert lib.cme_step(None, 1e-3, 1) == -1
