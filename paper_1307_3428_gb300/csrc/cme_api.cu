@@ -776,23 +776,27 @@ LargeArgs large_args(cme_batch b, const LaunchGroup& g)
     return a;
 }
 
-cudaError_t large_row(cme_batch b, const LaunchGroup& g, LargeArgs a, cudaStream_t st)
+// pdl: the kernel follows another row or column kernel of the same group in the stream and
+// may start while it finishes (programmatic dependent launch; the kernels order themselves).
+cudaError_t large_row(cme_batch b, const LaunchGroup& g, LargeArgs a, cudaStream_t st,
+                      bool pdl = false)
 {
     a.G = g.G2;
     ++g_launches;
     const long long rows = (long long)g.count << g.logN1;
-    return b->prec == PREC_FP64 ? launch_large_row_fp64(g.logN2, a, rows, st)
-                                : launch_large_row_fp32(g.logN2, a, rows, st);
+    return b->prec == PREC_FP64 ? launch_large_row_fp64(g.logN2, a, rows, st, pdl)
+                                : launch_large_row_fp32(g.logN2, a, rows, st, pdl);
 }
 
-cudaError_t large_col(cme_batch b, const LaunchGroup& g, LargeArgs a, int stage, cudaStream_t st)
+cudaError_t large_col(cme_batch b, const LaunchGroup& g, LargeArgs a, int stage, cudaStream_t st,
+                      bool pdl = false)
 {
     a.G = g.G1;
     a.stage = stage;
     ++g_launches;
     const long long cols = (long long)g.count << g.logN2;
-    return b->prec == PREC_FP64 ? launch_large_col_fp64(g.logN1, a, cols, st)
-                                : launch_large_col_fp32(g.logN1, a, cols, st);
+    return b->prec == PREC_FP64 ? launch_large_col_fp64(g.logN1, a, cols, st, pdl)
+                                : launch_large_col_fp32(g.logN1, a, cols, st, pdl);
 }
 
 // One RK4IP step of a four-step group: [row, col] for each of the four stages; the last column
@@ -800,9 +804,9 @@ cudaError_t large_col(cme_batch b, const LaunchGroup& g, LargeArgs a, int stage,
 cudaError_t large_one_step(cme_batch b, const LaunchGroup& g, const LargeArgs& a, cudaStream_t st)
 {
     for (int stage = 0; stage < 4; ++stage) {
-        cudaError_t e = large_row(b, g, a, st);
+        cudaError_t e = large_row(b, g, a, st, true);
         if (e == cudaSuccess)
-            e = large_col(b, g, a, stage, st);
+            e = large_col(b, g, a, stage, st, true);
         if (e != cudaSuccess)
             return e;
     }

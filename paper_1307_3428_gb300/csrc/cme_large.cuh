@@ -55,6 +55,14 @@ struct LargeArgs {
     void* diag_out;          // [ninst][N] transform order (rhs) or time order (idft)
 };
 
+// Programmatic dependent launch: the step's kernels are launched so that each may start while
+// its predecessor finishes.  A kernel reads only constant data (propagators, twiddles) before
+// pdl_wait(), which returns once the predecessor has completed and its writes are visible; every
+// read of mutable data and every write comes after it.  pdl_trigger() after the wait lets the
+// successor start its own constant prologue.  Launched without the attribute, both are no-ops.
+CME_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+CME_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Row pass: instance i = row / N1, row j1 = row mod N1.
 template <typename T, int LOGN2, int R>
 __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(const LargeArgs A)
@@ -76,6 +84,13 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
     grp.setup(smem, g, threadIdx.x - g * P, A.tw2);
     const int t = grp.t;
     const long long ibase = (long long)inst * N;   // offset of this instance in Y / Z
+    // the output twiddles (constant) before the wait, so that their latency overlaps it
+    cx<T> w[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        w[j] = gload<T>(A.twN, ((long long)j1 * (t + j * P)) & (N - 1));
+    pdl_wait();
+    pdl_trigger();
     const cx<T>* yrow = reinterpret_cast<const cx<T>*>(A.Y) + ibase + (long long)j1 * N2 + t;
     cx<T> x[R];
 #pragma unroll
@@ -96,11 +111,8 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
     cx<T>* zcol = reinterpret_cast<cx<T>*>(A.Z) + ibase + (long long)t * N1 + j1;
     if (valid) {
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const int m2 = t + j * P;
-            const cx<T> w = gload<T>(A.twN, ((long long)j1 * m2) & (N - 1));
-            zcol[(long long)j * P * N1] = cmulc(x[j], w);   // * exp(-2 pi i j1 m2 / N)
-        }
+        for (int j = 0; j < R; ++j)
+            zcol[(long long)j * P * N1] = cmulc(x[j], w[j]);   // * exp(-2 pi i j1 m2 / N)
     }
 }
 
@@ -131,6 +143,49 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     const long long estride = P;
     const long long f0 = A.base + e0;   // same element in the field / per-mode arrays
 
+    cx<T>* hi = reinterpret_cast<cx<T>*>(A.hi) + f0;
+    cx<T>* lo = reinterpret_cast<cx<T>*>(A.lo) + f0;
+    cx<T>* Sp = reinterpret_cast<cx<T>*>(A.S) + f0;
+    const cx<T>* Ep = reinterpret_cast<const cx<T>*>(A.E) + f0;
+    const cx<T>* e1p = reinterpret_cast<const cx<T>*>(A.e1) + f0;
+    const cx<T>* e2p = reinterpret_cast<const cx<T>*>(A.e2) + f0;
+    const int st = A.stage;
+    // Every operand of the Runge-Kutta combination and the output twiddles are loaded here,
+    // before the transforms, so that their latency overlaps the first transform: the constant
+    // ones (propagators, twiddles) even before the wait for the preceding kernel.
+    cx<T> Dh[R], Dl[R], Sv[R], Ev[R], ev[R], w[R];
+    const bool rk = A.diag != LDIAG_RHS;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const long long o = j * estride;
+        Dh[j] = Dl[j] = Sv[j] = Ev[j] = ev[j] = w[j] = cx<T>{T(0), T(0)};
+        if (rk) {
+            if (st >= 0 && st <= 2)
+                Ev[j] = gload<T>(Ep, o);
+            if (st == 0 || st == 1)
+                ev[j] = gload<T>(e1p, o);
+            else if (st == 2 || st == 3)
+                ev[j] = gload<T>(e2p, o);
+            if (st != LARGE_FINAL)
+                w[j] = gload<T>(A.twN, ((long long)(t + j * P) * m2) & (N - 1));
+        }
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (rk) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const long long o = j * estride;
+            Dh[j] = hi[o];
+            if (st >= 1 && st <= 3)
+                Sv[j] = Sp[o];
+            if constexpr (COMP) {
+                if (st == 3)
+                    Dl[j] = lo[o];
+            }
+        }
+    }
+
     cx<T> x[R];
     if (A.stage != LARGE_START) {
         // forward transform over j1 of Z column m2, as conj(inverse(conj(.)))
@@ -158,12 +213,6 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
             return;
         }
     }
-    cx<T>* hi = reinterpret_cast<cx<T>*>(A.hi) + f0;
-    cx<T>* lo = reinterpret_cast<cx<T>*>(A.lo) + f0;
-    cx<T>* Sp = reinterpret_cast<cx<T>*>(A.S) + f0;
-    const cx<T>* Ep = reinterpret_cast<const cx<T>*>(A.E) + f0;
-    const cx<T>* e1p = reinterpret_cast<const cx<T>*>(A.e1) + f0;
-    const cx<T>* e2p = reinterpret_cast<const cx<T>*>(A.e2) + f0;
     T h, hh, h6;
     if constexpr (sizeof(T) == 4) {
         h = A.hf;
@@ -174,45 +223,41 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
         hh = 0.5 * A.h;
         h6 = A.h / 6.0;
     }
-    const int st = A.stage;
     // Runge-Kutta combination of stage st (same increment form as rk4ip_step) and the next
     // stage's input; LARGE_START only loads D, LARGE_FINAL finishes the step without going on.
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         const long long o = j * estride;
-        cx<T> Dh = hi[o];
+        cx<T> D = Dh[j];
         if (st == LARGE_START) {
-            x[j] = Dh;
+            x[j] = D;
         } else if (st == 0) {
-            const cx<T> E = gload<T>(Ep, o);
-            const cx<T> k1 = cmul(E, x[j]);
-            Sp[o] = cmul(E, k1);
-            x[j] = cadd(Dh, caxpy(cmul(gload<T>(e1p, o), Dh), hh, k1));
+            const cx<T> k1 = cmul(Ev[j], x[j]);
+            Sp[o] = cmul(Ev[j], k1);
+            x[j] = cadd(D, caxpy(cmul(ev[j], D), hh, k1));
         } else if (st == 1) {
-            Sp[o] = caxpy(Sp[o], T(2), cmul(gload<T>(Ep, o), x[j]));
-            x[j] = cadd(Dh, caxpy(cmul(gload<T>(e1p, o), Dh), hh, x[j]));
+            Sp[o] = caxpy(Sv[j], T(2), cmul(Ev[j], x[j]));
+            x[j] = cadd(D, caxpy(cmul(ev[j], D), hh, x[j]));
         } else if (st == 2) {
-            const cx<T> Ek3 = cmul(gload<T>(Ep, o), x[j]);
-            Sp[o] = caxpy(Sp[o], T(2), Ek3);
-            x[j] = cadd(Dh, caxpy(cmul(gload<T>(e2p, o), Dh), h, Ek3));
+            const cx<T> Ek3 = cmul(Ev[j], x[j]);
+            Sp[o] = caxpy(Sv[j], T(2), Ek3);
+            x[j] = cadd(D, caxpy(cmul(ev[j], D), h, Ek3));
         } else {
-            const cx<T> e2 = gload<T>(e2p, o);
-            cx<T> Dl = {T(0), T(0)};
+            const cx<T> e2 = ev[j];
+            cx<T> L = Dl[j];
+            cx<T> d = cmul(e2, D);
             if constexpr (COMP)
-                Dl = lo[o];
-            cx<T> d = cmul(e2, Dh);
-            if constexpr (COMP)
-                d = cadd(d, cmul(e2, Dl));
-            d = caxpy(d, h6, cadd(Sp[o], x[j]));
-            accumulate<T, COMP>(Dh, Dl, d);
+                d = cadd(d, cmul(e2, L));
+            d = caxpy(d, h6, cadd(Sv[j], x[j]));
+            accumulate<T, COMP>(D, L, d);
             if (valid) {
-                hi[o] = Dh;
+                hi[o] = D;
                 if constexpr (COMP)
-                    lo[o] = Dl;
-                if (!(isfinite(Dh.re) && isfinite(Dh.im)))
+                    lo[o] = L;
+                if (!(isfinite(D.re) && isfinite(D.im)))
                     A.status[inst] = 1;
             }
-            x[j] = Dh;
+            x[j] = D;
         }
     }
     if (st == LARGE_FINAL)
@@ -222,11 +267,8 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     if (valid) {
         cx<T>* y = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)t * N2 + m2;
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const int j1 = t + j * P;
-            const cx<T> w = gload<T>(A.twN, ((long long)j1 * m2) & (N - 1));
-            y[(long long)j * P * N2] = cmul(x[j], w);      // * exp(+2 pi i j1 m2 / N)
-        }
+        for (int j = 0; j < R; ++j)
+            y[(long long)j * P * N2] = cmul(x[j], w[j]);   // * exp(+2 pi i j1 m2 / N)
     }
 }
 

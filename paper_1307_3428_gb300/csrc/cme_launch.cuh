@@ -63,6 +63,28 @@ inline cudaError_t launch_clustered(KernelT k, int blocks, int threads, size_t s
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
+// Launch with programmatic stream serialisation (pdl = true): the kernel may start before its
+// predecessor in the stream has finished, and orders itself with griddepcontrol.wait.
+template <typename KernelT, typename ArgT>
+inline cudaError_t launch_pdl(KernelT k, unsigned blocks, unsigned threads, size_t smem,
+                              cudaStream_t s, bool pdl, const ArgT& a)
+{
+    cudaError_t e = prepare_smem(k, smem);
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 template <typename T, int LOGN, int R, int C, int METHOD>
 inline cudaError_t launch_cluster_step_shape(const StepArgs& a, cudaStream_t s)
 {

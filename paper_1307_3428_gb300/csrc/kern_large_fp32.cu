@@ -6,7 +6,8 @@ namespace cme {
 
 #define CME_LARGE_SHAPES(X) X(6, 8) X(7, 8) X(8, 8) X(9, 8) X(10, 8)
 
-cudaError_t launch_large_row_fp32(int logN2, const LargeArgs& a, long long rows, cudaStream_t s)
+cudaError_t launch_large_row_fp32(int logN2, const LargeArgs& a, long long rows, cudaStream_t s,
+                                  bool pdl)
 {
     switch (logN2) {
 #define CME_CASE(LN, RR)                                                          \
@@ -14,11 +15,7 @@ cudaError_t launch_large_row_fp32(int logN2, const LargeArgs& a, long long rows,
         constexpr int P = Plan<LN, RR>::P;                                        \
         const size_t smem = smem_bytes_for<float>(LN, RR, a.G);                    \
         auto k = large_row_kernel<float, LN, RR>;                                  \
-        cudaError_t e = prepare_smem(k, smem);                                    \
-        if (e != cudaSuccess)                                                     \
-            return e;                                                             \
-        k<<<(unsigned)((rows + a.G - 1) / a.G), P * a.G, smem, s>>>(a);           \
-        return cudaGetLastError();                                                \
+        return launch_pdl(k, (unsigned)((rows + a.G - 1) / a.G), P * a.G, smem, s, pdl, a); \
     }
         CME_LARGE_SHAPES(CME_CASE)
 #undef CME_CASE
@@ -27,7 +24,8 @@ cudaError_t launch_large_row_fp32(int logN2, const LargeArgs& a, long long rows,
     }
 }
 
-cudaError_t launch_large_col_fp32(int logN1, const LargeArgs& a, long long cols, cudaStream_t s)
+cudaError_t launch_large_col_fp32(int logN1, const LargeArgs& a, long long cols, cudaStream_t s,
+                                  bool pdl)
 {
     switch (logN1) {
 #define CME_CASE(LN, RR)                                                          \
@@ -35,11 +33,7 @@ cudaError_t launch_large_col_fp32(int logN1, const LargeArgs& a, long long cols,
         constexpr int P = Plan<LN, RR>::P;                                        \
         const size_t smem = smem_bytes_for<float>(LN, RR, a.G);                    \
         auto k = large_col_kernel<float, LN, RR>;                                  \
-        cudaError_t e = prepare_smem(k, smem);                                    \
-        if (e != cudaSuccess)                                                     \
-            return e;                                                             \
-        k<<<(unsigned)((cols + a.G - 1) / a.G), P * a.G, smem, s>>>(a);           \
-        return cudaGetLastError();                                                \
+        return launch_pdl(k, (unsigned)((cols + a.G - 1) / a.G), P * a.G, smem, s, pdl, a); \
     }
         CME_LARGE_SHAPES(CME_CASE)
 #undef CME_CASE
