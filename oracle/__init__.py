@@ -54,28 +54,35 @@ def _load():
             lib = ctypes.CDLL(_LIB_PATH)
             dp = ctypes.POINTER(ctypes.c_double)
             c_int, c_long, c_double = ctypes.c_int, ctypes.c_long, ctypes.c_double
-            lib.oracle_fwm.argtypes = [c_int, c_int, dp, dp]
-            lib.oracle_rhs.argtypes = [c_int, c_int, c_double, c_double, c_double, c_double, dp, dp]
-            lib.oracle_integrate.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double,
+            lib.oracle_fwm.argtypes = [c_int, c_int, c_int, dp, dp]
+            lib.oracle_rhs.argtypes = [c_int, c_int, c_int, c_double, c_double, c_double, c_double,
+                                       dp, dp]
+            lib.oracle_integrate.argtypes = [c_int, c_int, c_int, c_int, dp, dp, c_double, c_double,
                                              c_double, c_double, c_double, c_double, c_long, dp]
             lib.oracle_integrate_eq1.argtypes = [c_int, c_int, dp, dp, c_double, c_double,
                                                  c_double, c_double, c_double, c_double,
                                                  c_double, c_long, dp]
             lib.oracle_dft.argtypes = [c_int, c_int, dp, dp]
             lib.oracle_invariants.argtypes = [c_int, c_int, dp, c_double, c_double, dp, dp]
-            lib.oracle_rk4ip_grad.argtypes = [c_int, c_int, dp, dp, c_double, c_double, c_double,
+            lib.oracle_rk4ip_grad.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
                                               c_double, c_double, c_double, c_long, dp, dp,
                                               c_double, dp, dp, dp, dp, dp]
-            lib.oracle_rk4ip_loss.argtypes = [c_int, c_int, dp, dp, c_double, c_double, c_double,
+            lib.oracle_rk4ip_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
                                               c_double, c_double, c_double, c_long, dp, dp,
                                               c_double, dp]
-            lib.oracle_fwm_vjp.argtypes = [c_int, c_int, dp, dp, dp]
+            lib.oracle_fwm_vjp.argtypes = [c_int, c_int, c_int, dp, dp, dp]
             for name in ("oracle_fwm", "oracle_rhs", "oracle_integrate", "oracle_integrate_eq1",
                          "oracle_dft", "oracle_invariants", "oracle_rk4ip_grad",
                          "oracle_rk4ip_loss", "oracle_fwm_vjp"):
                 getattr(lib, name).restype = c_int
             _lib = lib
     return _lib
+
+
+def _modes(inst) -> int:
+    """Physical mode count M of an instance (the centred M of its N modes; default N)."""
+    M = getattr(inst, "M", None)
+    return int(M) if M else int(inst.N)
 
 
 def _cbuf(z) -> np.ndarray:
@@ -92,21 +99,23 @@ def _check(rc: int):
         raise ValueError(f"oracle call failed with code {rc}")
 
 
-def fwm(D, linear: bool = False) -> np.ndarray:
-    """Direct FWM sum (Eq. 2 / Eq. 3) of a centred complex vector."""
+def fwm(D, linear: bool = False, M: int | None = None) -> np.ndarray:
+    """Direct FWM sum (Eq. 2 / Eq. 3) of a centred complex vector; M = physical modes (the
+    centred M of the N; default all), the others treated as padding."""
     d = _cbuf(D)
     N = d.size // 2
     out = np.empty_like(d)
-    _check(_load().oracle_fwm(N, int(linear), _dp(d), _dp(out)))
+    _check(_load().oracle_fwm(N, int(linear), int(M or N), _dp(d), _dp(out)))
     return out.view(np.complex128)
 
 
-def rhs(D, g0: float, kappa_ext: float, A_in: complex, linear: bool = False) -> np.ndarray:
+def rhs(D, g0: float, kappa_ext: float, A_in: complex, linear: bool = False,
+        M: int | None = None) -> np.ndarray:
     """F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D)."""
     d = _cbuf(D)
     N = d.size // 2
     out = np.empty_like(d)
-    _check(_load().oracle_rhs(N, int(linear), g0, kappa_ext, complex(A_in).real,
+    _check(_load().oracle_rhs(N, int(linear), int(M or N), g0, kappa_ext, complex(A_in).real,
                               complex(A_in).imag, _dp(d), _dp(out)))
     return out.view(np.complex128)
 
@@ -119,9 +128,9 @@ def integrate(inst, h: float, nsteps: int, method: int = RK4IP, linear: bool = F
     kap = np.ascontiguousarray(inst.kappa, dtype=np.float64)
     om = np.ascontiguousarray(inst.omega, dtype=np.float64)
     A = complex(inst.A_in)
-    _check(_load().oracle_integrate(method, inst.N, int(linear), _dp(kap), _dp(om), inst.g0,
-                                    inst.kappa_ext, A.real, A.imag, inst.sigma, h, int(nsteps),
-                                    _dp(d)))
+    _check(_load().oracle_integrate(method, inst.N, int(linear), _modes(inst), _dp(kap), _dp(om),
+                                    inst.g0, inst.kappa_ext, A.real, A.imag, inst.sigma, h,
+                                    int(nsteps), _dp(d)))
     return d.view(np.complex128)
 
 
@@ -156,13 +165,13 @@ def invariants(D, omega, g0: float, sigma: float, linear: bool = False):
     return float(out[0]), float(out[1])
 
 
-def fwm_vjp(D, Wbar, linear: bool = False) -> np.ndarray:
+def fwm_vjp(D, Wbar, linear: bool = False, M: int | None = None) -> np.ndarray:
     """J^H Wbar of the direct FWM sum at D (cotangent convention dL/dRe + i dL/dIm)."""
     d = _cbuf(D)
     wb = _cbuf(Wbar)
     N = d.size // 2
     out = np.empty_like(d)
-    _check(_load().oracle_fwm_vjp(N, int(linear), _dp(d), _dp(wb), _dp(out)))
+    _check(_load().oracle_fwm_vjp(N, int(linear), int(M or N), _dp(d), _dp(wb), _dp(out)))
     return out.view(np.complex128)
 
 
@@ -175,7 +184,7 @@ def log_spectrum_loss(inst, h: float, nsteps: int, target, eps: float = 1e-20,
     T = np.ascontiguousarray(target, dtype=np.float64)
     A = complex(inst.A_in)
     out = np.zeros(1)
-    _check(_load().oracle_rk4ip_loss(inst.N, int(linear), _dp(kap), _dp(om), inst.g0,
+    _check(_load().oracle_rk4ip_loss(inst.N, int(linear), _modes(inst), _dp(kap), _dp(om), inst.g0,
                                      inst.kappa_ext, A.real, A.imag, inst.sigma, h, int(nsteps),
                                      _dp(d), _dp(T), eps, _dp(out)))
     return float(out[0])
@@ -198,7 +207,8 @@ def log_spectrum_grad(inst, h: float, nsteps: int, target, eps: float = 1e-20,
     gLi = np.zeros(N)
     gLr = np.zeros(N)
     gP = np.zeros(2)
-    _check(_load().oracle_rk4ip_grad(N, int(linear), _dp(kap), _dp(om), inst.g0, inst.kappa_ext,
+    _check(_load().oracle_rk4ip_grad(N, int(linear), _modes(inst), _dp(kap), _dp(om), inst.g0,
+                                     inst.kappa_ext,
                                      A.real, A.imag, inst.sigma, h, int(nsteps), _dp(d), _dp(T),
                                      eps, _dp(loss), _dp(gD0), _dp(gLi), _dp(gLr), _dp(gP)))
     mu = np.arange(N) - N // 2

@@ -22,6 +22,12 @@
  *     FWM_mu(D) = sum_{alpha - beta + gamma = mu} D_alpha conj(D_beta) D_gamma.
  * The constraint alpha - beta + gamma = mu is taken modulo N ("circular", the reading that
  * matches Eq. 4 with an N-point transform) or literally ("linear", no wrap-around).
+ *
+ * Physical modes (the zero padding of Sec. 2: 201 modes in a 256-point transform): of the N
+ * modes only the M centred ones, mu = -floor(M/2) .. M - floor(M/2) - 1, are physical.  The
+ * others are held at zero: the FWM sum runs over physical alpha, beta, gamma only and is
+ * evaluated on physical mu only, and the Strang Kerr step is followed by zeroing them.
+ * M = N is the unpadded system.
  */
 #include <complex.h>
 #include <math.h>
@@ -56,15 +62,31 @@ static void store(int N, const cplx* in, double* out)
     }
 }
 
-/* Eq. 2 / Eq. 3: direct sum over (beta, gamma) with alpha = mu + beta - gamma. */
-static void fwm_direct(int N, int linear, const cplx* D, cplx* out)
+/* Is centred index i (mu = i - N/2) one of the M physical modes? */
+static int physical(int i, int N, int M)
+{
+    const int first = N / 2 - M / 2;
+    return i >= first && i < first + M;
+}
+
+/* Eq. 2 / Eq. 3: direct sum over (beta, gamma) with alpha = mu + beta - gamma, over the M
+ * physical modes. */
+static void fwm_direct(int N, int linear, int M, const cplx* D, cplx* out)
 {
     const int h = N / 2;
     for (int mu = -h; mu < N - h; ++mu) {
         cplx s = 0.0;
+        if (!physical(mu + h, N, M)) {
+            out[mu + h] = 0.0;
+            continue;
+        }
         for (int beta = -h; beta < N - h; ++beta) {
+            if (!physical(beta + h, N, M))
+                continue;
             const cplx cb = conj(D[beta + h]);
             for (int gamma = -h; gamma < N - h; ++gamma) {
+                if (!physical(gamma + h, N, M))
+                    continue;
                 long alpha = (long)mu + beta - gamma;
                 int ia;
                 if (linear) {
@@ -74,6 +96,8 @@ static void fwm_direct(int N, int linear, const cplx* D, cplx* out)
                 } else {
                     ia = wrap_index(alpha, N);
                 }
+                if (!physical(ia, N, M))
+                    continue;
                 s += D[ia] * cb * D[gamma + h];
             }
         }
@@ -84,6 +108,7 @@ static void fwm_direct(int N, int linear, const cplx* D, cplx* out)
 typedef struct {
     int N;
     int linear;
+    int M;   /* physical modes (N: all) */
     const double* kappa;
     const double* omega;
     double g0;
@@ -95,7 +120,7 @@ typedef struct {
 /* F(D) = pump + i g0 FWM(D) */
 static void rhs_nonlinear(const model* m, const cplx* D, cplx* out)
 {
-    fwm_direct(m->N, m->linear, D, out);
+    fwm_direct(m->N, m->linear, m->M, D, out);
     for (int i = 0; i < m->N; ++i)
         out[i] *= I * m->g0;
     out[m->N / 2] += sqrt(m->kappa_ext) * m->A_in;
@@ -222,7 +247,7 @@ static void step_strang(const model* m, double h, cplx* D, cplx* w)
     }
     dft_time_to_modes(N, a, D);
     for (int i = 0; i < N; ++i)
-        D[i] /= (double)N;
+        D[i] = physical(i, N, m->M) ? D[i] / (double)N : 0.0;
     linear_substep(m, 0.5 * h, D);
 }
 
@@ -237,25 +262,25 @@ static int check_model(int N, const double* kappa, const double* omega)
  * Exported entry points (plain doubles; complex arrays interleaved re, im).
  * ------------------------------------------------------------------------------------- */
 
-int oracle_fwm(int N, int linear, const double* D, double* out)
+int oracle_fwm(int N, int linear, int M, const double* D, double* out)
 {
-    if (N < 1 || !D || !out)
+    if (N < 1 || M < 1 || M > N || !D || !out)
         return ORACLE_EINVAL;
     cplx* d = malloc(sizeof(cplx) * 2 * N);
     load(N, D, d);
-    fwm_direct(N, linear, d, d + N);
+    fwm_direct(N, linear, M, d, d + N);
     store(N, d + N, out);
     free(d);
     return ORACLE_OK;
 }
 
 /* F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D) */
-int oracle_rhs(int N, int linear, double g0, double kappa_ext, double ain_re, double ain_im,
-               const double* D, double* out)
+int oracle_rhs(int N, int linear, int M, double g0, double kappa_ext, double ain_re,
+               double ain_im, const double* D, double* out)
 {
-    if (N < 1 || !D || !out)
+    if (N < 1 || M < 1 || M > N || !D || !out)
         return ORACLE_EINVAL;
-    model m = {N, linear, NULL, NULL, g0, kappa_ext, ain_re + I * ain_im, 0.0};
+    model m = {N, linear, M, NULL, NULL, g0, kappa_ext, ain_re + I * ain_im, 0.0};
     cplx* d = malloc(sizeof(cplx) * 2 * N);
     load(N, D, d);
     rhs_nonlinear(&m, d, d + N);
@@ -265,18 +290,22 @@ int oracle_rhs(int N, int linear, double g0, double kappa_ext, double ain_re, do
 }
 
 /* method: 0 = RK4IP, 1 = Strang, 2 = plain RK4.  D (2N doubles) is advanced in place. */
-int oracle_integrate(int method, int N, int linear, const double* kappa, const double* omega,
-                     double g0, double kappa_ext, double ain_re, double ain_im, double sigma,
-                     double h, long nsteps, double* D)
+int oracle_integrate(int method, int N, int linear, int M, const double* kappa,
+                     const double* omega, double g0, double kappa_ext, double ain_re,
+                     double ain_im, double sigma, double h, long nsteps, double* D)
 {
-    if (check_model(N, kappa, omega) || !D || nsteps < 0 || method < 0 || method > 2)
+    if (check_model(N, kappa, omega) || !D || nsteps < 0 || method < 0 || method > 2 || M < 1 ||
+        M > N)
         return ORACLE_EINVAL;
     if (method == 1 && linear)
         return ORACLE_EINVAL;
-    model m = {N, linear, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    model m = {N, linear, M, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
     cplx* d = malloc(sizeof(cplx) * N);
     cplx* w = malloc(sizeof(cplx) * 8 * N);
     load(N, D, d);
+    for (int i = 0; i < N; ++i)   /* padding modes start (and stay) at zero */
+        if (!physical(i, N, M))
+            d[i] = 0.0;
     for (long n = 0; n < nsteps; ++n) {
         if (method == 0)
             step_rk4ip(&m, h, d, w);
@@ -328,7 +357,7 @@ int oracle_integrate_eq1(int N, int linear, const double* kappa, const double* o
 {
     if (check_model(N, kappa, omega) || !A || nsteps < 0)
         return ORACLE_EINVAL;
-    model m = {N, linear, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    model m = {N, linear, N, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
     cplx* a = malloc(sizeof(cplx) * 6 * N);
     cplx *k1 = a + N, *k2 = a + 2 * N, *k3 = a + 3 * N, *k4 = a + 4 * N, *x = a + 5 * N;
     load(N, A, a);
@@ -380,7 +409,7 @@ int oracle_invariants(int N, int linear, const double* omega, double g0, double 
         return ORACLE_EINVAL;
     cplx* d = malloc(sizeof(cplx) * 2 * N);
     load(N, D, d);
-    fwm_direct(N, linear, d, d + N);
+    fwm_direct(N, linear, N, d, d + N);
     double norm = 0.0, quad = 0.0;
     cplx quart = 0.0;
     for (int i = 0; i < N; ++i) {
@@ -410,31 +439,47 @@ int oracle_invariants(int N, int linear, const double* omega, double g0, double 
  * over all steps, L_mu = -kappa_mu/2 + i(omega_mu - omega_0 - sigma)) and gP (cotangent of the
  * pump sqrt(kappa_ext) A_in).
  * ------------------------------------------------------------------------------------- */
-static int idx_of(long alpha, int N, int linear)
+/* centred index of alpha (wrapped or linear), or -1 if it is not a physical mode */
+static int idx_of(long alpha, int N, int linear, int M)
 {
     const int h = N / 2;
+    int i;
     if (linear) {
         if (alpha < -h || alpha >= N - h)
             return -1;
-        return (int)(alpha + h);
+        i = (int)(alpha + h);
+    } else {
+        i = wrap_index(alpha, N);
     }
-    return wrap_index(alpha, N);
+    return physical(i, N, M) ? i : -1;
 }
 
-static void fwm_vjp(int N, int linear, const cplx* D, const cplx* Wbar, cplx* Dbar)
+/* Over physical modes only: mu, nu, beta, gamma and the derived index all physical (the FWM
+ * sum of the padded system does not depend on the padding modes, nor does it feed them). */
+static void fwm_vjp(int N, int linear, int M, const cplx* D, const cplx* Wbar, cplx* Dbar)
 {
     const int h = N / 2;
     for (int nu = -h; nu < N - h; ++nu) {
         cplx s = 0.0;
+        if (!physical(nu + h, N, M)) {
+            Dbar[nu + h] = 0.0;
+            continue;
+        }
         for (int mu = -h; mu < N - h; ++mu) {
+            if (!physical(mu + h, N, M))
+                continue;
             const cplx w = Wbar[mu + h];
             for (int beta = -h; beta < N - h; ++beta) {
-                const int i = idx_of((long)mu + beta - nu, N, linear);
+                if (!physical(beta + h, N, M))
+                    continue;
+                const int i = idx_of((long)mu + beta - nu, N, linear, M);
                 if (i >= 0)
                     s += 2.0 * w * D[beta + h] * conj(D[i]);
             }
             for (int gamma = -h; gamma < N - h; ++gamma) {
-                const int i = idx_of((long)mu + nu - gamma, N, linear);
+                if (!physical(gamma + h, N, M))
+                    continue;
+                const int i = idx_of((long)mu + nu - gamma, N, linear, M);
                 if (i >= 0)
                     s += conj(w) * D[i] * D[gamma + h];
             }
@@ -450,20 +495,20 @@ static void rhs_vjp(const model* m, const cplx* x, const cplx* ybar, cplx* xbar,
     const int N = m->N;
     for (int i = 0; i < N; ++i)
         tmp[i] = conj(I * m->g0) * ybar[i];
-    fwm_vjp(N, m->linear, x, tmp, tmp + N);
+    fwm_vjp(N, m->linear, m->M, x, tmp, tmp + N);
     for (int i = 0; i < N; ++i)
         xbar[i] += tmp[N + i];
     *pbar += ybar[N / 2];
 }
 
-int oracle_rk4ip_grad(int N, int linear, const double* kappa, const double* omega, double g0,
-                      double kappa_ext, double ain_re, double ain_im, double sigma, double h,
-                      long nsteps, const double* D0, const double* target, double eps,
+int oracle_rk4ip_grad(int N, int linear, int M, const double* kappa, const double* omega,
+                      double g0, double kappa_ext, double ain_re, double ain_im, double sigma,
+                      double h, long nsteps, const double* D0, const double* target, double eps,
                       double* loss, double* gD0, double* gLi, double* gLr, double* gP)
 {
-    if (check_model(N, kappa, omega) || !D0 || !target || nsteps < 0 || !loss)
+    if (check_model(N, kappa, omega) || !D0 || !target || nsteps < 0 || !loss || M < 1 || M > N)
         return ORACLE_EINVAL;
-    model m = {N, linear, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    model m = {N, linear, M, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
     cplx* traj = malloc(sizeof(cplx) * N * (size_t)(nsteps + 1));
     cplx* w = malloc(sizeof(cplx) * 24 * N);
     cplx *E = w, *y1 = w + N, *k1 = w + 2 * N, *k2 = w + 3 * N, *k3 = w + 4 * N,
@@ -472,6 +517,9 @@ int oracle_rk4ip_grad(int N, int linear, const double* kappa, const double* omeg
          *wb = w + 14 * N, *xb = w + 15 * N, *vb = w + 16 * N, *ub = w + 17 * N,
          *kb = w + 18 * N, *Eb = w + 19 * N, *tmp = w + 20 * N; /* tmp uses 2N */
     load(N, D0, traj);
+    for (int i = 0; i < N; ++i)   /* padding modes start at zero, whatever D0 holds there */
+        if (!physical(i, N, M))
+            traj[i] = 0.0;
     cplx* sw = malloc(sizeof(cplx) * 8 * N);
     for (long n = 0; n < nsteps; ++n) {
         memcpy(traj + (size_t)(n + 1) * N, traj + (size_t)n * N, sizeof(cplx) * N);
@@ -553,6 +601,9 @@ int oracle_rk4ip_grad(int N, int linear, const double* kappa, const double* omeg
             Db[i] = Dp[i];
         }
     }
+    for (int i = 0; i < N; ++i)   /* D0 at the padding modes is overwritten by zero */
+        if (!physical(i, N, M))
+            Db[i] = 0.0;
     store(N, Db, gD0);
     gP[0] = creal(pbar);
     gP[1] = cimag(pbar);
@@ -562,17 +613,17 @@ int oracle_rk4ip_grad(int N, int linear, const double* kappa, const double* omeg
 }
 
 /* Loss of the forward RK4IP run alone (for finite differences). */
-int oracle_rk4ip_loss(int N, int linear, const double* kappa, const double* omega, double g0,
-                      double kappa_ext, double ain_re, double ain_im, double sigma, double h,
-                      long nsteps, const double* D0, const double* target, double eps,
+int oracle_rk4ip_loss(int N, int linear, int M, const double* kappa, const double* omega,
+                      double g0, double kappa_ext, double ain_re, double ain_im, double sigma,
+                      double h, long nsteps, const double* D0, const double* target, double eps,
                       double* loss)
 {
     if (check_model(N, kappa, omega) || !D0 || !target || !loss)
         return ORACLE_EINVAL;
     double* d = malloc(sizeof(double) * 2 * N);
     memcpy(d, D0, sizeof(double) * 2 * N);
-    int rc = oracle_integrate(0, N, linear, kappa, omega, g0, kappa_ext, ain_re, ain_im, sigma, h,
-                              nsteps, d);
+    int rc = oracle_integrate(0, N, linear, M, kappa, omega, g0, kappa_ext, ain_re, ain_im, sigma,
+                              h, nsteps, d);
     double L = 0.0;
     for (int i = 0; i < N; ++i) {
         const double P = d[2 * i] * d[2 * i] + d[2 * i + 1] * d[2 * i + 1];
@@ -585,14 +636,14 @@ int oracle_rk4ip_loss(int N, int linear, const double* kappa, const double* omeg
 }
 
 /* J^H w for the FWM map at D (exposed for the dot-product test). */
-int oracle_fwm_vjp(int N, int linear, const double* D, const double* Wbar, double* Dbar)
+int oracle_fwm_vjp(int N, int linear, int M, const double* D, const double* Wbar, double* Dbar)
 {
-    if (N < 1 || !D || !Wbar || !Dbar)
+    if (N < 1 || M < 1 || M > N || !D || !Wbar || !Dbar)
         return ORACLE_EINVAL;
     cplx* d = malloc(sizeof(cplx) * 3 * N);
     load(N, D, d);
     load(N, Wbar, d + N);
-    fwm_vjp(N, linear, d, d + N, d + 2 * N);
+    fwm_vjp(N, linear, M, d, d + N, d + 2 * N);
     store(N, d + 2 * N, Dbar);
     free(d);
     return ORACLE_OK;

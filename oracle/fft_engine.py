@@ -39,12 +39,23 @@ def fwm(D, linear: bool = False):
     return Y[..., mu % M]
 
 
+def physical_mask(N: int, M: int) -> np.ndarray:
+    """True on the M centred physical modes, mu = -floor(M/2) .. M - floor(M/2) - 1."""
+    first = N // 2 - M // 2
+    m = np.zeros(N, dtype=bool)
+    m[first:first + M] = True
+    return m
+
+
 class Batch:
-    """Per-instance parameters stacked for vectorised stepping."""
+    """Per-instance parameters stacked for vectorised stepping.  Instances may carry M, their
+    physical mode count: the other modes are held at zero and their FWM term is dropped."""
 
     def __init__(self, instances):
         self.N = instances[0].N
         assert all(i.N == self.N for i in instances)
+        self.mask = np.stack([physical_mask(self.N, getattr(i, "M", None) or self.N)
+                              for i in instances])
         self.kappa = np.stack([np.asarray(i.kappa, dtype=np.float64) for i in instances])
         self.omega = np.stack([np.asarray(i.omega, dtype=np.float64) for i in instances])
         self.g0 = np.array([i.g0 for i in instances])[:, None]
@@ -52,17 +63,19 @@ class Batch:
         self.sigma = np.array([i.sigma for i in instances])[:, None]
         om0 = self.omega[:, self.N // 2][:, None]
         self.L = -0.5 * self.kappa + 1j * (self.omega - om0 - self.sigma)
-        self.D0 = np.stack([np.asarray(i.D0, dtype=np.complex128) for i in instances])
+        self.D0 = np.where(self.mask, np.stack([np.asarray(i.D0, dtype=np.complex128)
+                                                for i in instances]), 0.0)
 
     def F(self, D, linear=False):
-        out = 1j * self.g0 * fwm(D, linear)
+        out = 1j * self.g0 * fwm(np.where(self.mask, D, 0.0), linear)
+        out = np.where(self.mask, out, 0.0)
         out[:, self.N // 2] += self.pump
         return out
 
 
 def rk4ip(batch: Batch, h: float, nsteps: int, D=None, linear: bool = False):
     """RK4IP (Hult 2007), E = exp(L h/2), same algebra as the direct engine."""
-    D = (batch.D0 if D is None else np.asarray(D)).astype(np.complex128, copy=True)
+    D = np.where(batch.mask, batch.D0 if D is None else np.asarray(D), 0.0).astype(np.complex128)
     E = np.exp(batch.L * (0.5 * h))
     for _ in range(nsteps):
         AI = E * D
@@ -76,8 +89,9 @@ def rk4ip(batch: Batch, h: float, nsteps: int, D=None, linear: bool = False):
 
 def strang(batch: Batch, h: float, nsteps: int, D=None):
     """Strang split step: exact linear+pump half step, exact Kerr phase rotation of the
-    time-domain field a (da/dtau = i g0 |a|^2 a), exact linear+pump half step."""
-    D = (batch.D0 if D is None else np.asarray(D)).astype(np.complex128, copy=True)
+    time-domain field a (da/dtau = i g0 |a|^2 a) followed by zeroing the padding modes, exact
+    linear+pump half step."""
+    D = np.where(batch.mask, batch.D0 if D is None else np.asarray(D), 0.0).astype(np.complex128)
     N = batch.N
     e = np.exp(batch.L * (0.5 * h))
     L0 = batch.L[:, N // 2]
@@ -88,7 +102,7 @@ def strang(batch: Batch, h: float, nsteps: int, D=None):
         D[:, N // 2] += c0
         a = np.fft.ifft(_to_fft(D), axis=-1) * N
         a = a * np.exp(1j * batch.g0 * np.abs(a) ** 2 * h)
-        D = _to_centred(np.fft.fft(a, axis=-1) / N)
+        D = np.where(batch.mask, _to_centred(np.fft.fft(a, axis=-1) / N), 0.0)
         D = e * D
         D[:, N // 2] += c0
     return D

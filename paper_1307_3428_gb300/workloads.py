@@ -41,6 +41,7 @@ class Instance:
     A_in: complex
     sigma: float
     D0: np.ndarray          # (N,) complex128 initial field
+    M: Optional[int] = None  # physical modes (the centred M of the N); None: all N
 
     @property
     def mu(self) -> np.ndarray:
