@@ -106,6 +106,16 @@ int cme_create(int N, const double* kappa_mu, const double* omega_mu, double g0,
 /* Set the initial rotating-frame field D_mu(0): 2N doubles, interleaved, centred order. */
 int cme_set_field(cme_instance inst, const double* D0);
 
+/* Number of physical modes M (1 <= M <= N; default N): the zero padding of Sec. 2, where 201
+ * modes run in a 256-point transform.  Of the N modes only the centred M,
+ * mu = -floor(M/2) .. M - floor(M/2) - 1, are physical.  The others are padding: they start
+ * at zero (whatever the field set for them) and stay there, and the four-wave-mixing sum runs
+ * over physical modes only and has no term on padding modes.  With N >= 2M no index triple wraps
+ * around into the physical band, and the sum is the linear (non-circular) sum of the M-mode
+ * system; M < N < 2M is the paper's own padding, where some triples still wrap.  The kappa,
+ * omega and field arrays keep N entries; padding entries are ignored.  Errors: INVALID_ARG. */
+int cme_set_modes(cme_instance inst, int M);
+
 void cme_destroy(cme_instance inst);
 
 /* ---- batches (device-resident sets of instances) --------------------------------------- */

@@ -65,6 +65,7 @@ _SIGS = [
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   ctypes.POINTER(_VP)]),
     ("cme_set_field", ctypes.c_int, [_VP, _DP]),
+    ("cme_set_modes", ctypes.c_int, [_VP, ctypes.c_int]),
     ("cme_destroy", None, [_VP]),
     ("cme_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int,
                                         ctypes.POINTER(Options), _VP, ctypes.POINTER(_VP)]),
@@ -157,7 +158,7 @@ def use_torch_allocator():
 class Instance:
     """Host-side parameters of one CME problem (see cme_create)."""
 
-    def __init__(self, N, kappa, omega, g0, kappa_ext, A_in, sigma, D0=None):
+    def __init__(self, N, kappa, omega, g0, kappa_ext, A_in, sigma, D0=None, M=None):
         lib = load()
         kap = np.ascontiguousarray(kappa, dtype=np.float64)
         om = np.ascontiguousarray(omega, dtype=np.float64)
@@ -169,11 +170,17 @@ class Instance:
         self.N = int(N)
         if D0 is not None:
             self.set_field(D0)
+        if M is not None:
+            self.set_modes(M)
 
     @classmethod
     def from_workload(cls, inst) -> "Instance":
         return cls(inst.N, inst.kappa, inst.omega, inst.g0, inst.kappa_ext, inst.A_in,
-                   inst.sigma, inst.D0)
+                   inst.sigma, inst.D0, getattr(inst, "M", None))
+
+    def set_modes(self, M: int):
+        """Physical mode count (cme_set_modes): the centred M of the N modes."""
+        _check(load().cme_set_modes(self.handle, int(M)))
 
     def set_field(self, D0):
         d = _interleave(D0)

@@ -93,8 +93,10 @@ __device__ __forceinline__ int centred_of(int q, int N)
     return (pm + N / 2) & (N - 1);
 }
 
+// inst_M (may be null): per-instance physical mode count; padding modes are set to zero.
 __global__ void import_kernel(int prec, int total, const int* mode_inst, const int* inst_N,
-                              const long long* inst_off, const double2* src, void* hi, void* lo)
+                              const long long* inst_off, const int* inst_M, const double2* src,
+                              void* hi, void* lo)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= total)
@@ -102,7 +104,13 @@ __global__ void import_kernel(int prec, int total, const int* mode_inst, const i
     const int i = mode_inst[m];
     const int N = inst_N[i];
     const long long off = inst_off[i];
-    const double2 v = src[off + centred_of((int)(m - off), N)];
+    const int c = centred_of((int)(m - off), N);
+    double2 v = src[off + c];
+    if (inst_M) {
+        const int M = inst_M[i], first = N / 2 - M / 2;
+        if (c < first || c >= first + M)
+            v = make_double2(0.0, 0.0);
+    }
     if (prec == PREC_FP64) {
         reinterpret_cast<double2*>(hi)[m] = v;
     } else {
@@ -304,11 +312,11 @@ cudaError_t launch_propagators(const PropArgs& a, cudaStream_t s)
 }
 
 cudaError_t launch_import(int prec, int total, const int* mode_inst, const int* inst_N,
-                          const long long* inst_off, const double2* src, void* hi, void* lo,
-                          cudaStream_t s)
+                          const long long* inst_off, const int* inst_M, const double2* src,
+                          void* hi, void* lo, cudaStream_t s)
 {
     import_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N, inst_off,
-                                                       src, hi, lo);
+                                                       inst_M, src, hi, lo);
     return cudaGetLastError();
 }
 

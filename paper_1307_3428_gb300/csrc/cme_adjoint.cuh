@@ -87,6 +87,8 @@ CME_DEV int adj_setup(Group<T, LOGN, R, C>& grp, unsigned char* smem, const Step
         inst = blockIdx.x / C;
         grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw);
     }
+    if (a.phys)
+        grp.set_modes(a.phys[inst]);
     return inst;
 }
 
@@ -209,6 +211,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 z[j] = {gNn * cot[j].im, -gNn * cot[j].re};
+            grp.mask(z);   // F is zero on padding modes: their cotangent does not enter
 #pragma unroll 1
             for (int p = 0; p < 2; ++p) {
                 if (p == 1) {
@@ -224,6 +227,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                 }
                 grp.inverse(z);
             }
+            grp.mask(z);   // nor does F depend on them: the VJP of m F(m x), m the mask
             // z now holds conj(stage-input cotangent)
 #pragma unroll
             for (int j = 0; j < R; ++j) {

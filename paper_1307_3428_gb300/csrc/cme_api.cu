@@ -126,6 +126,7 @@ int default_radix(int logN, int prec) { return logN <= 2 ? 4 : (logN == 12 && pr
 
 struct cme_instance_s {
     int N = 0;
+    int M = 0;   // physical modes (0: all N)
     std::vector<double> kappa, omega, field;
     double g0 = 0, kappa_ext = 0, ain_re = 0, ain_im = 0, sigma = 0;
 };
@@ -137,6 +138,7 @@ struct LaunchGroup {
     long long base = 0;         // first mode offset
     int R = 8, G = 1;
     int C = 1;                  // blocks per instance (thread-block cluster when > 1)
+    bool masked = false;        // some instance has padding modes (M < N)
     // N > 4096: four-step split N = N1 N2 (column length N1, row length N2)
     bool large = false;
     int logN1 = 0, logN2 = 0, G1 = 1, G2 = 1;
@@ -166,6 +168,7 @@ struct cme_batch_s {
     double *kappa = nullptr, *omega = nullptr, *sigma_d = nullptr, *g0_d = nullptr;
     double2 *pump_d = nullptr, *cpump_d = nullptr, *stage = nullptr;
     int *mode_inst = nullptr, *inst_N = nullptr, *status_d = nullptr;
+    int* phys_d = nullptr;   // per-instance physical mode count M
     long long* inst_off = nullptr;
     std::map<int, void*> tw;  // per log2 N
 
@@ -407,6 +410,16 @@ int cme_set_field(cme_instance inst, const double* D0)
     return CME_OK;
 }
 
+int cme_set_modes(cme_instance inst, int M)
+{
+    if (!inst)
+        return fail(CME_ERR_INVALID_ARG, "cme_set_modes: NULL instance");
+    if (M < 1 || M > inst->N)
+        return fail(CME_ERR_INVALID_ARG, "cme_set_modes: M=%d outside [1, N=%d]", M, inst->N);
+    inst->M = M;
+    return CME_OK;
+}
+
 void cme_destroy(cme_instance inst) { delete inst; }
 
 void cme_batch_destroy(cme_batch b)
@@ -569,6 +582,7 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     b->cpump_d = (double2*)A(count * 16);
     b->inst_N = (int*)A(count * 4);
     b->status_d = (int*)A(count * 4);
+    b->phys_d = (int*)A(count * 4);
     b->inst_off = (long long*)A(count * 8);
     for (auto& g : b->groups) {
         if (!b->tw.count(g.logN))
@@ -633,6 +647,14 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     CPY(b->g0_d, g0.data(), count * 8);
     CPY(b->pump_d, pump.data(), count * 16);
     CPY(b->inst_N, b->N_h.data(), count * 4);
+    std::vector<int> Mh(count);
+    for (int i = 0; i < count; ++i)
+        Mh[i] = v[i]->M > 0 ? v[i]->M : v[i]->N;
+    CPY(b->phys_d, Mh.data(), count * 4);
+    for (auto& g : b->groups)
+        for (int i = g.first; i < g.first + g.count; ++i)
+            if (Mh[i] < g.N)
+                g.masked = true;
     CPY(b->inst_off, b->off_h.data(), count * 8);
     CPY(b->stage, field.data(), T * 16);
 #undef CPY
@@ -644,8 +666,8 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         }
     }
     if (e == cudaSuccess) {
-        e = launch_import(b->prec, (int)T, b->mode_inst, b->inst_N, b->inst_off, b->stage, b->hi,
-                          b->lo, s);
+        e = launch_import(b->prec, (int)T, b->mode_inst, b->inst_N, b->inst_off, b->phys_d,
+                          b->stage, b->hi, b->lo, s);
         ++g_launches;
     }
     if (e == cudaSuccess)
@@ -722,6 +744,7 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
     a.cpump = b->cpump_d + g.first;
     a.g0 = b->g0_d + g.first;
     a.status = b->status_d + g.first;
+    a.phys = g.masked ? b->phys_d + g.first : nullptr;   // null: no padding modes in the group
     a.h = b->h_cur;
     a.hf = (float)b->h_cur;
     a.hhf = (float)(0.5 * b->h_cur);
@@ -769,6 +792,7 @@ LargeArgs large_args(cme_batch b, const LaunchGroup& g)
     a.pump = b->pump_d + g.first;
     a.g0 = b->g0_d + g.first;
     a.status = b->status_d + g.first;
+    a.phys = g.masked ? b->phys_d + g.first : nullptr;   // null: no padding modes in the group
     a.h = b->h_cur;
     a.hf = (float)b->h_cur;
     a.hhf = (float)(0.5 * b->h_cur);
@@ -1309,8 +1333,8 @@ int cme_set_state(cme_batch b, const double* buf, int where)
         src = b->stage;
     }
     ++g_launches;
-    CME_CUDA(launch_import(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, src, b->hi,
-                           b->lo, b->stream),
+    CME_CUDA(launch_import(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off,
+                           b->phys_d, src, b->hi, b->lo, b->stream),
              "cme_set_state: import");
     CME_CUDA(cudaMemsetAsync(b->status_d, 0, b->count * 4, b->stream), "cme_set_state: status");
     if (where == CME_HOST)

@@ -26,6 +26,7 @@ struct StepArgs {
     const double2* cpump;   // per-instance Strang pump increment over h/2
     const double* g0;       // per-instance Kerr coefficient g0
     int* status;            // per-instance status (group-relative)
+    const int* phys;        // per-instance physical mode count M (group-relative; null: all N)
     long long nsteps;
     double h;
     float hf, hhf, h6f;     // h, h/2, h/6 rounded once to FP32 on the host
@@ -64,6 +65,12 @@ cudaError_t launch_step_fp64_rk4ip(int logN, int R, const StepArgs& a, cudaStrea
 cudaError_t launch_step_fp64_strang(int logN, int R, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp32_rk4ip(int logN, int R, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp32_strang(int logN, int R, const StepArgs& a, cudaStream_t s);
+// The same with the physical-mode mask compiled in (a.phys set); the launchers above forward
+// to these when a.phys is not null.
+cudaError_t launch_step_fp64_rk4ip_masked(int logN, int R, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp64_strang_masked(int logN, int R, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp32_rk4ip_masked(int logN, int R, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp32_strang_masked(int logN, int R, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_diag_fp64(int logN, int R, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_diag_fp32(int logN, int R, const StepArgs& a, cudaStream_t s);
 
@@ -91,10 +98,11 @@ struct PropArgs {
 };
 cudaError_t launch_propagators(const PropArgs& a, cudaStream_t s);
 cudaError_t launch_twiddles(int N, int prec, void* out, cudaStream_t s);
-// Centred FP64 <-> internal transform-order field (optionally split into hi/lo).
+// Centred FP64 <-> internal transform-order field (optionally split into hi/lo).  inst_M (may
+// be null): per-instance physical mode count; import sets the padding modes to zero.
 cudaError_t launch_import(int prec, int total, const int* mode_inst, const int* inst_N,
-                          const long long* inst_off, const double2* src, void* hi, void* lo,
-                          cudaStream_t s);
+                          const long long* inst_off, const int* inst_M, const double2* src,
+                          void* hi, void* lo, cudaStream_t s);
 cudaError_t launch_export(int prec, int total, const int* mode_inst, const int* inst_N,
                           const long long* inst_off, const void* hi, const void* lo,
                           double2* dst, int what, const double* omega, const double* sigma,

@@ -48,6 +48,7 @@ struct LargeArgs {
     const double2* pump;     // per instance (group-relative)
     const double* g0;
     int* status;
+    const int* phys;         // per-instance physical mode count M (null: all N)
     double h;
     float hf, hhf, h6f;
     int stage;               // col kernel: LARGE_START, 0..3, LARGE_FINAL
@@ -199,6 +200,20 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
 #pragma unroll
         for (int j = 0; j < R; ++j)
             x[j].im = -x[j].im;
+        if (A.phys) {
+            // padding modes (outside the centred M physical ones) get no FWM term
+            const int M = A.phys[inst];
+            if (M < N) {
+                const long long mlo = -(M / 2), mhi = M - M / 2 - 1;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const long long m = (long long)(t + j * P) * N2 + m2;   // mode mu mod N
+                    const long long mu = m >= N / 2 ? m - N : m;
+                    if (mu < mlo || mu > mhi)
+                        x[j] = cx<T>{T(0), T(0)};
+                }
+            }
+        }
         if (t == 0 && m2 == 0) {
             const double2 pd = A.pump[inst];
             x[0] = cadd(x[0], cx<T>{(T)pd.x, (T)pd.y});

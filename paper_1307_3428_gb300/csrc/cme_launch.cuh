@@ -93,14 +93,15 @@ inline cudaError_t launch_cluster_step_shape(const StepArgs& a, cudaStream_t s)
                             Plan<LOGN, R>::P / C, cluster_smem_bytes<T, LOGN, R, C>(), C, s, a);
 }
 
-template <typename T, int LOGN, int R, int METHOD>
+// MASKABLE: the kernel applies the physical-mode mask of a.phys (launched when a.phys is set).
+template <typename T, int LOGN, int R, int METHOD, bool MASKABLE>
 inline cudaError_t launch_step_shape(const StepArgs& a, cudaStream_t s)
 {
     constexpr int P = Plan<LOGN, R>::P;
     const int threads = P * a.G;
     const int blocks = (a.ninst + a.G - 1) / a.G;
     const size_t smem = smem_bytes_for<T>(LOGN, R, a.G);
-    auto k = step_kernel<T, LOGN, R, METHOD>;
+    auto k = step_kernel<T, LOGN, R, METHOD, MASKABLE>;
     cudaError_t e = prepare_smem(k, smem);
     if (e != cudaSuccess)
         return e;

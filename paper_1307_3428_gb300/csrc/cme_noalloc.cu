@@ -172,7 +172,7 @@ extern "C" int cme_rk4ip_noalloc(int N, int count, double h, long nsteps, const 
         e = launch_propagators(p, s);
     }
     if (e == cudaSuccess)
-        e = launch_import(PREC_FP64, (int)total, mode_inst, inst_N, inst_off,
+        e = launch_import(PREC_FP64, (int)total, mode_inst, inst_N, inst_off, nullptr,
                           (const double2*)d_field, hi, nullptr, s);
     if (e == cudaSuccess && nsteps > 0) {
         int logN = 0;

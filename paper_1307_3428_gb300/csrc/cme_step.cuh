@@ -82,6 +82,36 @@ struct Group {
     Xbuf<T> buf;   // first of the two ping-pong exchange buffers
     typename TF::Addr ad;
     TW tw;
+    // Physical modes (the zero padding of Sec. 2): of the N modes only the centred M,
+    // mu = mlo .. mhi, are physical; the right-hand side is zero on the others, which stay at
+    // zero.  masked = false (M = N) skips the test.
+    bool masked;
+    int mlo, mhi;
+
+    CME_DEV void set_modes(int M)
+    {
+        masked = M < N;
+        mlo = -(M / 2);
+        mhi = M - M / 2 - 1;
+    }
+    // Is the thread's position t + jP (mode mu = p or p - N, transform order) physical?
+    CME_DEV bool physical(int j) const
+    {
+        if (!masked)
+            return true;
+        const int p = t + j * P;
+        const int mu = p >= N / 2 ? p - N : p;
+        return mu >= mlo && mu <= mhi;
+    }
+    CME_DEV void mask(cx<T> (&x)[R]) const
+    {
+        if (masked) {
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (!physical(j))
+                    x[j] = cx<T>{T(0), T(0)};
+        }
+    }
 
     // The step loops contain a single copy of the transform code (instruction-cache
     // footprint): the forward transform is computed as conj(inverse(conj(x))).
@@ -113,6 +143,7 @@ struct Group {
 #pragma unroll
         for (int j = 0; j < R; ++j)
             x[j].im = -x[j].im;
+        mask(x);
         if (t == 0)
             x[0] = cadd(x[0], pump);
     }
@@ -140,6 +171,7 @@ struct Group {
         par = 0;
         ad = TF::make_addr(t);
         tw.init(tw_table, t);
+        set_modes(N);
     }
 
     // Cluster set-up (C > 1): block `rank` of the cluster, thread l of the block; the block's
@@ -159,6 +191,7 @@ struct Group {
         par = 0;
         ad = TF::make_addr_cluster(t, l, smem_addr(smem));
         tw.init(tw_table, t);
+        set_modes(N);
     }
 };
 
@@ -386,6 +419,7 @@ CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
                     }
                 }
             }
+            grp.mask(x);   // no Kerr increment on padding modes
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 fs.add(j, cx<T>{x[j].re, -x[j].im});
@@ -422,7 +456,9 @@ CME_DEV StepConsts<T> step_consts(const StepArgs& a, int inst, int N)
 
 // nsteps steps of the instances [first, first + blockDim.x / P) of the group described by a
 // (group-relative indices; groups past a.ninst recompute the last instance and store nothing).
-template <typename T, int LOGN, int R, int METHOD>
+// MASKABLE = false compiles the body without the physical-mode mask (every instance M = N):
+// the mask test then folds away at compile time.
+template <typename T, int LOGN, int R, int METHOD, bool MASKABLE = true>
 CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
 {
     using GR = Group<T, LOGN, R>;
@@ -435,6 +471,10 @@ CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
         inst = a.ninst - 1;  // duplicate work keeps every group in the barriers; no store
     GR grp;
     grp.setup(smem, g, threadIdx.x - g * P, a.tw);
+    if constexpr (MASKABLE) {
+        if (a.phys)
+            grp.set_modes(a.phys[inst]);
+    }
     const int t = grp.t;
     const long long off = a.base + (long long)inst * N;
 
@@ -465,11 +505,11 @@ CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
     }
 }
 
-template <typename T, int LOGN, int R, int METHOD>
+template <typename T, int LOGN, int R, int METHOD, bool MASKABLE>
 __global__ void __launch_bounds__(max_threads<LOGN, R>()) step_kernel(const StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    step_body<T, LOGN, R, METHOD>(a, blockIdx.x * a.G, smem);
+    step_body<T, LOGN, R, METHOD, MASKABLE>(a, blockIdx.x * a.G, smem);
 }
 
 // The same steps with each instance spread over a cluster of C blocks (P/C threads each);
@@ -484,6 +524,8 @@ __global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(cons
     const int inst = blockIdx.x / C;
     GR grp;
     grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw);
+    if (a.phys)
+        grp.set_modes(a.phys[inst]);
     const int t = grp.t;
     const long long off = a.base + (long long)inst * N;
 
@@ -529,6 +571,8 @@ __global__ void __launch_bounds__(max_threads<LOGN, R>()) diag_kernel(const Step
         inst = a.ninst - 1;
     GR grp;
     grp.setup(smem, g, threadIdx.x - g * P, a.tw);
+    if (a.phys)
+        grp.set_modes(a.phys[inst]);
     const int t = grp.t;
     const long long off = a.base + (long long)inst * N;
     const cx<T>* src = reinterpret_cast<const cx<T>*>(a.hi) + off + t;

@@ -1,0 +1,20 @@
+// RK4IP step kernels, FP32, for groups with padding modes (physical-mode mask
+// compiled in): explicit instantiations and the shape dispatch.
+#include "cme_launch.cuh"
+
+namespace cme {
+
+cudaError_t launch_step_fp32_rk4ip_masked(int logN, int R, const StepArgs& a, cudaStream_t s)
+{
+    switch (logN * 32 + R) {
+#define CME_CASE(LN, RR) \
+    case LN * 32 + RR:   \
+        return launch_step_shape<float, LN, RR, METHOD_RK4IP, true>(a, s);
+        CME_FOR_EACH_SHAPE(CME_CASE)
+#undef CME_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace cme

@@ -5,10 +5,12 @@ namespace cme {
 
 cudaError_t launch_step_fp32_strang(int logN, int R, const StepArgs& a, cudaStream_t s)
 {
+    if (a.phys)   // some instance of the group has padding modes
+        return launch_step_fp32_strang_masked(logN, R, a, s);
     switch (logN * 32 + R) {
 #define CME_CASE(LN, RR) \
     case LN * 32 + RR:   \
-        return launch_step_shape<float, LN, RR, METHOD_STRANG>(a, s);
+        return launch_step_shape<float, LN, RR, METHOD_STRANG, false>(a, s);
         CME_FOR_EACH_SHAPE(CME_CASE)
 #undef CME_CASE
     default:

@@ -177,6 +177,32 @@ def sech2_target(N: int, batch: int) -> np.ndarray:
     return out
 
 
+def fig1(f0_over_sqrt2: Sequence[float] = (1.01, 1.2, 1.8, 4.0), N: int = 256, M: int = 201,
+         nsteps: int = 32768, noise: float = 1e-4) -> Workload:
+    """Sec. 2, Fig. 1: the normalised Eq. 2 with N = 256 (201 physical modes zero padded to
+    2^8), Omega_mu = -0.00625 mu^2, kappa_mu = kappa_0, f0 = {1.01, 1.2, 1.8, 4} sqrt(2),
+    tau~ = 128 pi, split step.
+
+    Eq. 2 is the library's model with tau = tau~, kappa_mu = 2 (so -kappa_mu/2 = -1),
+    g0 = 1, sqrt(kappa_ext) A_in = f0 (kappa_ext = 1) and omega_mu - omega_0 - sigma = Omega_mu;
+    Omega_0 = 0 makes sigma = 0 with omega_mu = Omega_mu.  The paper states neither the step
+    nor the initial field: h = 128 pi / nsteps, and the stationary CW state of the pumped mode
+    (unique at zero detuning) plus seeded noise of RMS `noise` on every physical mode."""
+    mu = (np.arange(N) - N // 2).astype(np.float64)
+    om = -0.00625 * mu * mu
+    insts = []
+    for b, f in enumerate(f0_over_sqrt2):
+        f0 = float(f) * np.sqrt(2.0)
+        D0 = _noise(N, noise, seed=1307 + 1000 * 6 + b)
+        D0[N // 2] += cw_lower_branch(0.0, f0, 2.0, 1.0, 1.0)
+        insts.append(Instance(N=N, kappa=np.full(N, 2.0), omega=om.copy(), g0=1.0,
+                              kappa_ext=1.0, A_in=complex(f0), sigma=0.0,
+                              D0=D0.astype(np.complex128), M=M))
+    return Workload("fig1_n256_m201", insts, 128.0 * np.pi / nsteps, nsteps,
+                    "Fig. 1: N=256 (201 physical), Omega=-0.00625 mu^2, f0=(1.01,1.2,1.8,4)sqrt2, "
+                    "tau~=128 pi, Strang")
+
+
 def octave(N: int = 1 << 17, nsteps: int = 10000) -> Workload:
     """N=2^17 single instance: D2=2e-4, D3=-4e-7, sigma=4, A_in=3, noise 1e-8, h=1e-4."""
     inst = make_instance(N, 2e-4, -4e-7, 4.0, 3.0, 1e-8, seed=1307 + 1000 * 5 + 0)

@@ -79,6 +79,12 @@ def test_batch_create_rejects_bad_arguments(lib):
     with pytest.raises(cme.CmeError) as e:
         cme.Batch([a], radix=2)      # launch shape not compiled
     assert e.value.code == -1
+    for M in (0, 17, -3):            # physical modes must lie in [1, N]
+        with pytest.raises(cme.CmeError) as e:
+            a.set_modes(M)
+        assert e.value.code == -1 and b"cme_set_modes" in lib.cme_last_error()
+    a.set_modes(16)
+    a.set_modes(1)
     for c in (3, 16, -1):            # blocks per instance must be 0, 1, 2, 4 or 8
         with pytest.raises(cme.CmeError) as e:
             cme.Batch([a], cluster=c)
