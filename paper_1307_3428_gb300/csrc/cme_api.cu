@@ -947,9 +947,12 @@ cudaError_t enqueue_steps(cme_batch b, long nsteps, int* nk)
             e = launch_group_step(b, b->groups[0], n, b->stream);
             ++k;
         } else {
-            // fork the groups onto side streams so that they run concurrently, then join
+            // fork the groups onto side streams so that they run concurrently, then join.
+            // Largest N first: its kernel is the longest, and its blocks (one instance per SM
+            // at N = 4096) must not queue behind the persistent blocks of lighter groups.
             e = cudaEventRecord(b->ev[0], b->stream);
-            for (size_t i = 0; e == cudaSuccess && i < b->groups.size(); ++i) {
+            for (size_t r = 0; e == cudaSuccess && r < b->groups.size(); ++r) {
+                const size_t i = b->groups.size() - 1 - r;
                 e = cudaStreamWaitEvent(b->side[i], b->ev[0], 0);
                 if (e == cudaSuccess)
                     e = launch_group_step(b, b->groups[i], n, b->side[i]);
