@@ -117,10 +117,9 @@ bool shape_compiled(int logN, int R)
     return false;
 }
 
-// Values per thread: 8, except N = 4096 in FP32, where 16 values per thread (256 threads, up to
-// 255 registers) beat 8 (512 threads, at most 128 registers, spilling): 19.3 against 22.8 us
-// per step measured on GB300.
-int default_radix(int logN, int prec) { return logN <= 2 ? 4 : (logN == 12 && prec == PREC_FP32 ? 16 : 8); }
+// Values per thread: 8 (N = 4: 4).  With the twiddles of N >= 2048 in shared memory, 8 values
+// per thread also win at N = 4096 in FP32: 13.3 against 14.2 us per step at 16 (GB300).
+int default_radix(int logN, int) { return logN <= 2 ? 4 : 8; }
 
 }  // namespace
 

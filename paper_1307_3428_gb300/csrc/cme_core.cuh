@@ -513,6 +513,45 @@ struct Twiddles<T, LOGN, R, false> {
     }
 };
 
+// The same twiddles held in shared memory, each thread's in its own slots of a thread-major
+// array [(pass, butterfly, j)][P] (no bank conflicts; no thread reads another's slot, so no
+// barrier is needed after the fill).  Used where registers are too scarce and the table loads
+// would crowd the global-load queue (FP32, N >= 2048).
+template <typename T, int LOGN, int R>
+struct TwiddlesSmem {
+    using PL = Plan<LOGN, R>;
+    const cx<T>* base;   // this thread's slot 0
+
+    CME_DEV void init(const void* table, int t, cx<T>* smem_tw)
+    {
+        base = smem_tw + t;
+        init_from<1>(table, t, smem_tw);
+    }
+    template <int s>
+    CME_DEV void init_from(const void* table, int t, cx<T>* smem_tw)
+    {
+        if constexpr (s < PL::NS) {
+            constexpr int r = PL::radix(s), Q = R / r, L = PL::L(s);
+            constexpr int stride = PL::N / (L * r);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int k = (t + q * PL::P) & (L - 1);
+#pragma unroll
+                for (int j = 1; j < r; ++j)
+                    smem_tw[((s - 1) * (R - 1) + q * (r - 1) + (j - 1)) * PL::P + t] =
+                        gload<T>(table, (j * k * stride) & (PL::N - 1));
+            }
+            init_from<s + 1>(table, t, smem_tw);
+        }
+    }
+    template <int s>
+    CME_DEV cx<T> get(int q, int j) const
+    {
+        constexpr int r = PL::radix(s);
+        return base[((s - 1) * (R - 1) + q * (r - 1) + (j - 1)) * PL::P];
+    }
+};
+
 // Compensated update (hi, lo) += d with an exact two-sum of hi and (lo + d).
 template <typename T, bool COMP>
 CME_DEV void accumulate(cx<T>& hi, cx<T>& lo, cx<T> d)

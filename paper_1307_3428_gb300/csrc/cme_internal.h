@@ -35,17 +35,39 @@ struct StepArgs {
 };
 
 // Shared-memory footprint of one instance group (one instance of N = 2^logN handled by N/R
-// threads): two padded ping-pong exchange buffers, plus -- for wide groups whose registers are
-// scarce -- the Runge-Kutta accumulator S and (FP32) the compensation word of the field.
+// threads): two padded ping-pong exchange buffers; for wide groups whose registers are scarce,
+// the Runge-Kutta accumulator S and (FP32) the compensation word of the field; and, for FP32
+// groups of N >= 2048 (twiddles neither in registers nor read from the global table), each
+// thread's pass twiddles in thread-major order.
 __host__ __device__ constexpr bool acc_in_smem(int tbytes, int logN, int R)
 {
     return tbytes == 4 ? R >= 16 : logN >= 11;
 }
+__host__ __device__ constexpr bool twiddles_in_smem(int tbytes, int logN)
+{
+    return tbytes == 4 && logN >= 11;
+}
+__host__ __device__ constexpr int log2_radix(int R) { return R >= 16 ? 4 : R >= 8 ? 3 : R >= 4 ? 2 : 1; }
+__host__ __device__ constexpr size_t xbuf_bytes(int tbytes, int logN)
+{
+    return (size_t)2 * (tbytes == 4 ? 1 : 2) * ((1 << logN) + (1 << logN) / 16 + 1) * 8;
+}
+__host__ __device__ constexpr size_t acc_bytes(int tbytes, int logN, int R)
+{
+    return acc_in_smem(tbytes, logN, R) ? (size_t)(1 << logN) * 2 * tbytes * (tbytes == 4 ? 2 : 1)
+                                        : 0;
+}
+// (passes - 1) * (R - 1) twiddles per thread, N / R threads, 8-byte (FP32) complex values
+__host__ __device__ constexpr size_t tw_bytes(int tbytes, int logN, int R)
+{
+    return twiddles_in_smem(tbytes, logN)
+               ? (size_t)((logN + log2_radix(R) - 1) / log2_radix(R) - 1) * (R - 1) *
+                     ((1 << logN) / R) * 8
+               : 0;
+}
 __host__ __device__ constexpr size_t group_smem_bytes(int tbytes, int logN, int R)
 {
-    return (size_t)2 * (tbytes == 4 ? 1 : 2) * ((1 << logN) + (1 << logN) / 16 + 1) * 8 +
-           (acc_in_smem(tbytes, logN, R) ? (size_t)(1 << logN) * 2 * tbytes * (tbytes == 4 ? 2 : 1)
-                                         : 0);
+    return xbuf_bytes(tbytes, logN) + acc_bytes(tbytes, logN, R) + tw_bytes(tbytes, logN, R);
 }
 
 // Cluster launches: one instance spread over the C blocks of a thread-block cluster.  Compiled

@@ -2,6 +2,8 @@
 // RK4IP or Strang steps with the field held in registers throughout.
 #pragma once
 
+#include <type_traits>
+
 #include "cme_core.cuh"
 
 namespace cme {
@@ -75,7 +77,12 @@ struct Group {
     static constexpr bool WARP = (C == 1 && P <= 32);
     static constexpr bool COMP = (sizeof(T) == 4);  // compensated state in FP32
     using TF = Transform<T, LOGN, R, WARP, C>;
-    using TW = Twiddles<T, LOGN, R, twiddles_in_regs<T, LOGN>()>;
+    // twiddles: registers (small N), this group's shared memory (FP32 one-block groups of
+    // N >= 2048), else the global table
+    static constexpr bool TW_SMEM = C == 1 && !twiddles_in_regs<T, LOGN>() &&
+                                    twiddles_in_smem(sizeof(T), LOGN);
+    using TW = std::conditional_t<TW_SMEM, TwiddlesSmem<T, LOGN, R>,
+                                  Twiddles<T, LOGN, R, twiddles_in_regs<T, LOGN>()>>;
 
     int t;
     int par;
@@ -159,6 +166,7 @@ struct Group {
         unsigned char* gbase = smem + (size_t)g * group_smem_bytes(sizeof(T), LOGN, R);
         double* base = reinterpret_cast<double*>(gbase);
         cx<T>* acc = reinterpret_cast<cx<T>*>(gbase + (size_t)2 * W * PL::BUF * 8);
+        static_assert(xbuf_bytes(sizeof(T), LOGN) == (size_t)2 * W * PL::BUF * 8, "layout");
         accS = acc + t_;
         accL = acc + N + t_;
         if constexpr (sizeof(T) == 4) {
@@ -170,7 +178,12 @@ struct Group {
         t = t_;
         par = 0;
         ad = TF::make_addr(t);
-        tw.init(tw_table, t);
+        if constexpr (TW_SMEM)
+            tw.init(tw_table, t,
+                    reinterpret_cast<cx<T>*>(gbase + xbuf_bytes(sizeof(T), LOGN) +
+                                             acc_bytes(sizeof(T), LOGN, R)));
+        else
+            tw.init(tw_table, t);
         set_modes(N);
     }
 
