@@ -383,8 +383,12 @@ def run_gpu(args, world, rank, local):
             traffic = ent.get("dram_bytes_per_launch")
     if prec_main == cme.FP64:
         peak = FP64_NOMINAL_TFLOPS
+    # the same FMA rate measured by the library's FMA-chain microbenchmark (context: the
+    # derived peak above is the denominator)
+    fma_meas = cme.fma_peak(prec_main) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "measured_fma_tflops": fma_meas, "frac_of_measured_fma": achieved / fma_meas,
                 "kernel": (f"step_kernel<float, 9, {args.radix or 8}, RK4IP>" if headline
                            else f"{args.workload} step kernel(s)"),
                 "peak_basis": ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"

@@ -119,7 +119,18 @@ bool shape_compiled(int logN, int R)
 
 // Values per thread: 8 (N = 4: 4).  With the twiddles of N >= 2048 in shared memory, 8 values
 // per thread also win at N = 4096 in FP32: 13.3 against 14.2 us per step at 16 (GB300).
-int default_radix(int logN, int) { return logN <= 2 ? 4 : 8; }
+// FP64 groups too small to give every SM a warp at 8 values per thread take 4: each thread's
+// chain of FP64 instructions (1/64 of the FP32 rate) then sets the step time, and halving it
+// measured 31 against 55 us per step for one N = 64 instance.  sms = 0: no such information.
+int default_radix(int logN, int prec, int count = 0, int sms = 0)
+{
+    if (logN <= 2)
+        return 4;
+    if (prec == PREC_FP64 && sms > 0 && shape_compiled(logN, 4) &&
+        (long long)count * ((1 << logN) / 8) < 32LL * sms)
+        return 4;
+    return 8;
+}
 
 }  // namespace
 
@@ -274,7 +285,7 @@ int plan_batch(cme_batch b, const cme_options& o)
             any_large = true;
             continue;
         }
-        int R = o.radix ? o.radix : default_radix(g.logN, b->prec);
+        int R = o.radix ? o.radix : default_radix(g.logN, b->prec, g.count, b->sms);
         if (R > g.N)
             R = g.N;
         if (!shape_compiled(g.logN, R))
@@ -1583,15 +1594,10 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
     CME_CUDA(cudaMemsetAsync(b->g_pbar, 0, (size_t)b->count * 16, st), "cme_grad: zero");
     auto run_segment = [&](int role, long long sg, cudaStream_t str) -> cudaError_t {
         for (auto& g : b->groups) {
-            // The adjoint kernels address the field by mode position, so they need not share
-            // the forward plan's values per thread: they take 8 (their live state is larger
-            // than a forward step's; at N = 4096 FP32, 8 values per thread without spills beat
-            // 16: 66.5 against 74.4 us per gradient step).  Cluster groups keep their plan.
-            LaunchGroup ga = g;
-            if (g.C == 1) {
-                ga.R = std::min(default_radix(g.logN, PREC_FP64), g.N);
-                ga.G = inst_per_block(g.N, ga.R, 0, g.count);
-            }
+            // The adjoint kernels run the forward plan's values per thread, so that the
+            // recomputation reproduces the forward states bit for bit and the gradient does not
+            // depend on the segment length.
+            const LaunchGroup& ga = g;
             AdjArgs A{};
             A.s = group_args(b, ga);
             A.nsteps = nsteps;
