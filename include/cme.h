@@ -103,6 +103,19 @@ int cme_create(int N, const double* kappa_mu, const double* omega_mu, double g0,
                double kappa_ext, double A_in_re, double A_in_im, double sigma,
                cme_instance* out);
 
+/* Create an instance of the normalised Eq. 2 (Sec. 2):
+ *   dA~_mu/dtau~ = (-kappa_mu/kappa_0 + i Omega_mu) A~_mu + delta_{mu,0} f0
+ *                  + i sum_{alpha-beta+gamma=mu} A~_alpha A~*_beta A~_gamma,
+ * whose time is tau~ = kappa_0 tau / 2: h, nsteps and the accumulated time of cme_step are then
+ * in units of tau~, and the field is A~ (in the frame of Omega_mu, like D of cme_create).
+ *   kappa_rel  N values kappa_mu / kappa_0 (centred), each >= 0; NULL: all 1;
+ *   Omega      N normalised detunings Omega_mu (centred; Omega_0 is the pump detuning term);
+ *   f0         complex normalised pump.
+ * Equivalent to cme_create with kappa_mu = 2 kappa_rel, omega_mu = Omega_mu - Omega_0, g0 = 1,
+ * kappa_ext = 1, A_in = f0, sigma = -Omega_0.  Errors as cme_create. */
+int cme_create_eq2(int N, const double* kappa_rel, const double* Omega, double f0_re,
+                   double f0_im, cme_instance* out);
+
 /* Set the initial rotating-frame field D_mu(0): 2N doubles, interleaved, centred order. */
 int cme_set_field(cme_instance inst, const double* D0);
 

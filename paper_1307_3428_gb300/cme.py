@@ -64,6 +64,8 @@ _SIGS = [
     ("cme_create", ctypes.c_int, [ctypes.c_int, _DP, _DP, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   ctypes.POINTER(_VP)]),
+    ("cme_create_eq2", ctypes.c_int, [ctypes.c_int, _DP, _DP, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(_VP)]),
     ("cme_set_field", ctypes.c_int, [_VP, _DP]),
     ("cme_set_modes", ctypes.c_int, [_VP, ctypes.c_int]),
     ("cme_destroy", None, [_VP]),
@@ -172,6 +174,24 @@ class Instance:
             self.set_field(D0)
         if M is not None:
             self.set_modes(M)
+
+    @classmethod
+    def from_eq2(cls, N, Omega, f0, kappa_rel=None, D0=None, M=None) -> "Instance":
+        """An instance of the normalised Eq. 2 (cme_create_eq2)."""
+        self = cls.__new__(cls)
+        om = np.ascontiguousarray(Omega, dtype=np.float64)
+        kr = None if kappa_rel is None else np.ascontiguousarray(kappa_rel, dtype=np.float64)
+        h = ctypes.c_void_p()
+        f0 = complex(f0)
+        _check(load().cme_create_eq2(int(N), None if kr is None else _dptr(kr), _dptr(om),
+                                     f0.real, f0.imag, ctypes.byref(h)))
+        self.handle = h
+        self.N = int(N)
+        if D0 is not None:
+            self.set_field(D0)
+        if M is not None:
+            self.set_modes(M)
+        return self
 
     @classmethod
     def from_workload(cls, inst) -> "Instance":

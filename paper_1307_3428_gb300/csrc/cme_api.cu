@@ -409,6 +409,33 @@ int cme_create(int N, const double* kappa_mu, const double* omega_mu, double g0,
     return CME_OK;
 }
 
+int cme_create_eq2(int N, const double* kappa_rel, const double* Omega, double f0_re,
+                   double f0_im, cme_instance* out)
+{
+    if (!out)
+        return fail(CME_ERR_INVALID_ARG, "cme_create_eq2: out is NULL");
+    *out = nullptr;
+    if (!is_pow2(N) || N < 4 || N > (1 << 20))
+        return fail(CME_ERR_UNSUPPORTED_N, "cme_create_eq2: N=%d is not a power of two in [4, 2^20]",
+                    N);
+    if (!Omega)
+        return fail(CME_ERR_INVALID_ARG, "cme_create_eq2: Omega is required");
+    // Eq. 2 is Eq. 1 in the frame of the library with tau = tau~, kappa_mu = 2 kappa_mu/kappa_0,
+    // g0 = 1, sqrt(kappa_ext) A_in = f0 and omega_mu - omega_0 - sigma = Omega_mu
+    std::vector<double> kap(N), om(N);
+    const double O0 = Omega[N / 2];
+    for (int i = 0; i < N; ++i) {
+        kap[i] = 2.0 * (kappa_rel ? kappa_rel[i] : 1.0);
+        om[i] = Omega[i] - O0;
+    }
+    if (!std::isfinite(O0))
+        return fail(CME_ERR_INVALID_ARG, "cme_create_eq2: Omega_0 is not finite");
+    int rc = cme_create(N, kap.data(), om.data(), 1.0, 1.0, f0_re, f0_im, -O0, out);
+    if (rc != CME_OK)
+        g_err = "cme_create_eq2: " + g_err;
+    return rc;
+}
+
 int cme_set_field(cme_instance inst, const double* D0)
 {
     if (!inst || !D0)
@@ -538,23 +565,25 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         return fail(CME_ERR_INVALID_ARG, "cme_batch_create: more than %d distinct N", MAX_GROUPS);
     }
     // host-side validation of the launch options before any CUDA call
-    for (auto& g : b->groups) {
+    // (the group's fields are copied out before cme_batch_destroy frees the groups)
+    for (const auto& g : b->groups) {
+        const int N = g.N;
         if (g.large) {
             if (o.integrator != CME_RK4IP) {
                 cme_batch_destroy(b);
                 return fail(CME_ERR_INVALID_ARG,
-                            "cme_batch_create: N=%d > 4096 runs RK4IP only", g.N);
+                            "cme_batch_create: N=%d > 4096 runs RK4IP only", N);
             }
             continue;
         }
-        const int R = std::min(o.radix ? o.radix : default_radix(g.logN, b->prec), g.N);
+        const int R = std::min(o.radix ? o.radix : default_radix(g.logN, b->prec), N);
         if (!shape_compiled(g.logN, R) || o.persistent < 0 || o.persistent > 2 ||
             !(o.cluster == 0 || o.cluster == 1 || o.cluster == 2 || o.cluster == 4 ||
               o.cluster == 8)) {
             cme_batch_destroy(b);
             return fail(CME_ERR_INVALID_ARG,
                         "cme_batch_create: launch option (radix %d, persistent %d, cluster %d) "
-                        "not available for N=%d", R, o.persistent, o.cluster, g.N);
+                        "not available for N=%d", R, o.persistent, o.cluster, N);
         }
     }
     if (cuda_stream) {

@@ -112,3 +112,18 @@ def test_fp32_close_to_fp64(fp64_run):
     got = run(w, cme.FP32)
     for k, tol in ((0, 1e-4), (1, 1e-4), (2, 1e-3)):
         assert rel(got[k], ref[k]) <= tol, k
+
+
+def test_eq2_constructor_gives_the_same_run():
+    """cme_create_eq2 (the normalised Eq. 2 entry point) reproduces the workload's own mapping
+    of Fig. 1 onto Eq. 1 bit for bit."""
+    w = wl.fig1(f0_over_sqrt2=(1.2, 1.8))
+    # Omega_mu = -0.00625 mu^2, exactly the array the workload built (Omega_0 = 0)
+    via_eq2 = [cme.Instance.from_eq2(256, i.omega, i.A_in, D0=i.D0, M=201) for i in w.instances]
+    out = []
+    for insts in (via_eq2, [cme.Instance.from_workload(i) for i in w.instances]):
+        b = cme.Batch(insts, precision=cme.FP64, integrator=cme.STRANG)
+        b.step(w.h, 500)
+        out.append(b.get_state())
+        b.close()
+    assert np.array_equal(out[0], out[1])

@@ -78,13 +78,23 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert e.value.code == -1
     with pytest.raises(cme.CmeError) as e:
         cme.Batch([a], radix=2)      # launch shape not compiled
-    assert e.value.code == -1
+    assert e.value.code == -1 and b"N=16" in lib.cme_last_error()
     for M in (0, 17, -3):            # physical modes must lie in [1, N]
         with pytest.raises(cme.CmeError) as e:
             a.set_modes(M)
         assert e.value.code == -1 and b"cme_set_modes" in lib.cme_last_error()
     a.set_modes(16)
     a.set_modes(1)
+    out = ctypes.c_void_p()
+    om = np.zeros(16)
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert lib.cme_create_eq2(16, None, None, 1.0, 0.0, ctypes.byref(out)) == -1
+    assert lib.cme_create_eq2(12, None, om.ctypes.data_as(dp), 1.0, 0.0, ctypes.byref(out)) == -2
+    bad = np.full(16, -1.0)
+    assert lib.cme_create_eq2(16, bad.ctypes.data_as(dp), om.ctypes.data_as(dp), 1.0, 0.0,
+                              ctypes.byref(out)) == -1
+    assert b"cme_create_eq2" in lib.cme_last_error()
+    cme.Instance.from_eq2(16, om, 1.2 + 0.1j, M=11)
     for c in (3, 16, -1):            # blocks per instance must be 0, 1, 2, 4 or 8
         with pytest.raises(cme.CmeError) as e:
             cme.Batch([a], cluster=c)
