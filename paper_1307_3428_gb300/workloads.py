@@ -203,6 +203,24 @@ def fig1(f0_over_sqrt2: Sequence[float] = (1.01, 1.2, 1.8, 4.0), N: int = 256, M
                     "tau~=128 pi, Strang")
 
 
+def lle_instance(N: int, alpha: float, beta: float, F: complex, noise: float, seed: int,
+                 cw: bool = True) -> Instance:
+    """The normalised Lugiato-Lefever equation
+        d psi/d tau = -(1 + i alpha) psi + i |psi|^2 psi - i (beta/2) d^2 psi/d theta^2 + F
+    as a CME instance: psi(theta) = sum_mu A_mu exp(i mu theta) turns it into Eq. 2 with
+    kappa_mu = kappa_0, Omega_mu = -alpha + (beta/2) mu^2 and f0 = F, i.e. the library's model
+    with kappa_mu = 2, g0 = 1, kappa_ext = 1, A_in = F, omega_mu = (beta/2) mu^2 and
+    sigma = alpha.  Initial modes: the homogeneous stationary state (the lower CW branch) plus
+    seeded noise of RMS `noise` on every mode."""
+    mu = (np.arange(N) - N // 2).astype(np.float64)
+    D0 = _noise(N, noise, seed)
+    if cw:
+        D0[N // 2] += cw_lower_branch(alpha, F, 2.0, 1.0, 1.0)
+    return Instance(N=N, kappa=np.full(N, 2.0), omega=0.5 * beta * mu * mu, g0=1.0,
+                    kappa_ext=1.0, A_in=complex(F), sigma=float(alpha),
+                    D0=D0.astype(np.complex128))
+
+
 def octave(N: int = 1 << 17, nsteps: int = 10000) -> Workload:
     """N=2^17 single instance: D2=2e-4, D3=-4e-7, sigma=4, A_in=3, noise 1e-8, h=1e-4."""
     inst = make_instance(N, 2e-4, -4e-7, 4.0, 3.0, 1e-8, seed=1307 + 1000 * 5 + 0)
