@@ -117,8 +117,9 @@ bool shape_compiled(int logN, int R)
     return false;
 }
 
-// Values per thread: 8 (N = 4: 4).  With the twiddles of N >= 2048 in shared memory, 8 values
-// per thread also win at N = 4096 in FP32: 13.3 against 14.2 us per step at 16 (GB300).
+// Values per thread: 8 (N = 4: 4), except FP32 N >= 2048, which take 16: with their twiddles
+// in shared memory and their propagators in registers that measured 11.7 against 13.3 us per
+// step at N = 4096 and 7.2 against 7.4 at N = 2048 (GB300).
 // FP64 groups too small to give every SM a warp at 8 values per thread take 4: each thread's
 // chain of FP64 instructions (1/64 of the FP32 rate) then sets the step time, and halving it
 // measured 31 against 55 us per step for one N = 64 instance.  sms = 0: no such information.
@@ -126,6 +127,8 @@ int default_radix(int logN, int prec, int count = 0, int sms = 0)
 {
     if (logN <= 2)
         return 4;
+    if (prec == PREC_FP32 && logN >= 11)
+        return 16;
     if (prec == PREC_FP64 && sms > 0 && shape_compiled(logN, 4) &&
         (long long)count * ((1 << logN) / 8) < 32LL * sms)
         return 4;
@@ -1598,6 +1601,18 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
         return rc;
     const size_t fb = (size_t)b->total * b->elem;
     cudaStream_t st = b->stream;
+    // Launch plan of the gradient's forward, recomputation and backward kernels, shared so
+    // that the recomputation reproduces the forward states bit for bit.  FP32 takes 8 values
+    // per thread: the backward kernel's live state spills at 16 (N = 4096: 47.3 against 50.4
+    // us per gradient step with the forward at 16).  FP64 keeps the batch's plan.
+    std::vector<LaunchGroup> ag(b->groups);
+    for (auto& g : ag) {
+        g.chunk = nullptr;   // copies never own the chunk graphs
+        if (b->prec == PREC_FP32 && g.C == 1) {
+            g.R = g.N <= 4 ? 4 : 8;
+            g.G = inst_per_block(g.N, g.R, 0, g.count);
+        }
+    }
     // forward with checkpoints at the segment starts
     for (long long s = 0; s < S; ++s) {
         CME_CUDA(cudaMemcpyAsync((char*)b->g_ckpt_hi + s * fb, b->hi, fb, cudaMemcpyDeviceToDevice, st),
@@ -1607,7 +1622,8 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
                                      cudaMemcpyDeviceToDevice, st),
                      "cme_grad: checkpoint");
         const long long n = std::min(K, (long long)nsteps - s * K);
-        CME_CUDA(enqueue_steps(b, (long)n, nullptr), "cme_grad: forward");
+        for (auto& g : ag)
+            CME_CUDA(launch_group_step(b, g, n, st), "cme_grad: forward");
     }
     // loss and its seed
     CME_CUDA(cudaMemcpyAsync(b->g_target, target, (size_t)b->total * 8, cudaMemcpyHostToDevice, st),
@@ -1622,11 +1638,7 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
     CME_CUDA(cudaMemsetAsync(b->g_gL, 0, (size_t)b->total * 16, st), "cme_grad: zero");
     CME_CUDA(cudaMemsetAsync(b->g_pbar, 0, (size_t)b->count * 16, st), "cme_grad: zero");
     auto run_segment = [&](int role, long long sg, cudaStream_t str) -> cudaError_t {
-        for (auto& g : b->groups) {
-            // The adjoint kernels run the forward plan's values per thread, so that the
-            // recomputation reproduces the forward states bit for bit and the gradient does not
-            // depend on the segment length.
-            const LaunchGroup& ga = g;
+        for (const auto& ga : ag) {
             AdjArgs A{};
             A.s = group_args(b, ga);
             A.nsteps = nsteps;
@@ -1639,7 +1651,7 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
             A.stages = b->g_stages;
             A.dbar = b->g_dbar;
             A.gL = b->g_gL;
-            A.pbar = b->g_pbar + g.first;
+            A.pbar = b->g_pbar + ga.first;
             ++g_launches;
             cudaError_t e = b->prec == PREC_FP64
                                 ? launch_adjoint_fp64(role, ga.logN, ga.R, ga.C, A, str)

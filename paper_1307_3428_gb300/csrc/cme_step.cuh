@@ -19,8 +19,10 @@ constexpr int max_threads() { return Plan<LOGN, R>::P >= 64 ? Plan<LOGN, R>::P :
 // launch; otherwise they are read through the read-only cache where used.
 template <typename T, int LOGN, int R, int C = 1>
 struct Props {
-    // cluster groups run few threads per block, so their register budget has room
-    static constexpr bool IN_REGS = sizeof(T) == 4 && (LOGN <= 10 || C > 1) && R <= 8;
+    // cluster groups run few threads per block, so their register budget has room, and so do
+    // 16-value groups of N >= 2048, whose twiddles live in shared memory
+    static constexpr bool IN_REGS =
+        sizeof(T) == 4 && (((LOGN <= 10 || C > 1) && R <= 8) || (LOGN >= 11 && R == 16));
     cx<T> E[IN_REGS ? R : 1], e1[IN_REGS ? R : 1], e2[IN_REGS ? R : 1];
     const cx<T>* pE;   // pointers pre-offset to (instance offset + t)
     const cx<T>* pe1;
