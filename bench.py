@@ -334,33 +334,46 @@ def run_gpu(args, world, rank, local):
         one_step(b32)
     torch.cuda.synchronize()
 
-    sampler = ClockSampler(local)
-    launches0 = cme.kernel_launches()
-    k_ms = []
-    barrier(world)
-    torch.cuda.synchronize()
-    sampler.start()
-    t_wall0 = time.perf_counter()
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()                       # evict L2 between timed steps (not timed)
+    def timed_loop():
+        sampler = ClockSampler(local)
+        launches0 = cme.kernel_launches()
+        k_ms = []
+        barrier(world)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e2 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b32.set_state_device(d0_dev.data_ptr())
-        e1.record(stream)
-        b32.step(w.h, nsteps)
-        e2.record(stream)
-        e2.synchronize()
-        total_ms += e0.elapsed_time(e2)
-        k_ms.append(e1.elapsed_time(e2))
-    torch.cuda.synchronize()
-    barrier(world)
-    wall = time.perf_counter() - t_wall0
-    clocks = sampler.stop()
-    launches = cme.kernel_launches() - launches0
+        sampler.start()
+        t_wall0 = time.perf_counter()
+        total_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()                       # evict L2 between timed steps (not timed)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b32.set_state_device(d0_dev.data_ptr())
+            e1.record(stream)
+            b32.step(w.h, nsteps)
+            e2.record(stream)
+            e2.synchronize()
+            total_ms += e0.elapsed_time(e2)
+            k_ms.append(e1.elapsed_time(e2))
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t_wall0
+        return total_ms, k_ms, wall, sampler.stop(), cme.kernel_launches() - launches0
+
+    total_ms, k_ms, wall, clocks, launches = timed_loop()
+    # The clock record cannot show another context time-slicing this GPU.  The library's FMA
+    # microbenchmark can: far below the derived FMA peak (here once 21.7 of 80.5 TFLOP/s, with
+    # every step 4.8x slow and clocks at their maximum), the timing is repeated once.
+    fma_meas = cme.fma_peak(prec_main) / 1e12
+    fma_derived = (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12 if prec_main == cme.FP32
+                   else FP64_NOMINAL_TFLOPS)
+    retimed = False
+    if prec_main == cme.FP32 and fma_meas < 0.6 * fma_derived:
+        total_ms, k_ms, wall, clocks, launches = timed_loop()
+        fma_meas = cme.fma_peak(prec_main) / 1e12
+        retimed = True
     step_ms = max_over_ranks(total_ms / args.steps, world)
     value = world * mode_steps / (step_ms * 1e-3)
 
@@ -383,9 +396,8 @@ def run_gpu(args, world, rank, local):
             traffic = ent.get("dram_bytes_per_launch")
     if prec_main == cme.FP64:
         peak = FP64_NOMINAL_TFLOPS
-    # the same FMA rate measured by the library's FMA-chain microbenchmark (context: the
-    # derived peak above is the denominator)
-    fma_meas = cme.fma_peak(prec_main) / 1e12
+    # fma_meas: the same FMA rate measured by the library's FMA-chain microbenchmark (context:
+    # the derived peak above is the denominator)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "measured_fma_tflops": fma_meas, "frac_of_measured_fma": achieved / fma_meas,
@@ -480,6 +492,8 @@ def run_gpu(args, world, rank, local):
         "error": error,
         "wall_s_timed": wall,
     }
+    if retimed:
+        line["retimed_after_low_fma_rate"] = True
     if plan is not None:
         line["config"]["plan"] = plan
     if args.workload == "fig1":

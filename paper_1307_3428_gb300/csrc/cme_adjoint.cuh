@@ -95,8 +95,9 @@ CME_DEV int adj_setup(Group<T, LOGN, R, C>& grp, unsigned char* smem, const Step
 template <int LOGN, int R, int C>
 constexpr int adj_threads() { return C == 1 ? max_threads<LOGN, R>() : Plan<LOGN, R>::P / C; }
 
-// Recompute role: the states of segment A.seg from its checkpoint, and the stage values
-// y1, k2, k3 of every step, into half (A.seg mod 2) of A.stages.
+// Recompute role: the states of segment A.seg from its checkpoint, the stage values y1, k2, k3
+// and the time-domain fields of the four stage inputs of every step, into half (A.seg mod 2)
+// of A.stages.
 template <typename T, int LOGN, int R, int C = 1>
 __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(const AdjArgs A)
 {
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
 }
 
 // Backward role: the discrete adjoint of the steps of segment A.seg, last step first, from
-// the states and stage values in half (A.seg mod 2) of A.stages.  The field cotangent, the
+// the states, stage values and stage fields in half (A.seg mod 2) of A.stages.  The field cotangent, the
 // L cotangents and the pump cotangent are carried between segments in A.dbar, A.gL, A.pbar.
 template <typename T, int LOGN, int R, int C = 1>
 __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(const AdjArgs A)
