@@ -76,6 +76,8 @@ typedef struct cme_options {
                               at 8 values per thread: C > 1 spreads each instance over a
                               thread-block cluster whose blocks exchange through distributed
                               shared memory (one kernel per N group; also used by cme_grad).
+                              With radix 0, a cluster request selects the clusters' 8
+                              values per thread.
                               0 = library choice: FP64 batches take the largest C with
                               instances * C <= SMs (FP64 arithmetic is the bound, so more
                               SMs per instance pay); FP32 batches take C = 1 (their exchanges
@@ -148,6 +150,12 @@ int cme_batch_info(cme_batch b, int* count, long* total_modes, int* precision, i
 
 /* The batch's stream (cudaStream_t). */
 void* cme_batch_stream(cme_batch b);
+
+/* The launch plan the library chose for launch group `group` (0-based, groups in increasing N):
+ * N, values per thread, instances per block, blocks per instance (cluster) and the batch's
+ * persistent mode (1 or 2).  Any output pointer may be NULL.  Errors: INVALID_ARG. */
+int cme_batch_plan(cme_batch b, int group, int* N, int* radix, int* inst_per_cta, int* cluster,
+                   int* persistent);
 
 /* Advance every instance by nsteps steps of size h (> 0) of the batch's integrator (Sec. 2:
  * RK4 or split step, with the FWM term evaluated through Eq. 4).  Asynchronous.  The first

@@ -74,6 +74,7 @@ _SIGS = [
     ("cme_batch_destroy", None, [_VP]),
     ("cme_batch_info", ctypes.c_int, [_VP, _IP, ctypes.POINTER(ctypes.c_long), _IP, _IP]),
     ("cme_batch_stream", _VP, [_VP]),
+    ("cme_batch_plan", ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _IP, _IP, _IP]),
     ("cme_step", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long]),
     ("cme_synchronize", ctypes.c_int, [_VP]),
     ("cme_autotune", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long, ctypes.POINTER(Options)]),
@@ -256,6 +257,13 @@ class Batch:
 
     def synchronize(self):
         _check(load().cme_synchronize(self.handle))
+
+    def plan(self, group: int = 0) -> dict:
+        """The launch plan of one launch group (cme_batch_plan)."""
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(load().cme_batch_plan(self.handle, int(group), *[ctypes.byref(x) for x in v]))
+        return dict(zip(("N", "radix", "inst_per_cta", "cluster", "persistent"),
+                        (x.value for x in v)))
 
     def autotune(self, h: float, probe_steps: int = 200) -> dict:
         opt = Options()

@@ -289,6 +289,10 @@ int plan_batch(cme_batch b, const cme_options& o)
             continue;
         }
         int R = o.radix ? o.radix : default_radix(g.logN, b->prec, g.count, b->sms);
+        // an explicit cluster request without an explicit radix takes the clusters' 8 values
+        // per thread
+        if (!o.radix && o.cluster > 1 && cluster_shape_compiled(g.logN, 8, o.cluster))
+            R = 8;
         if (R > g.N)
             R = g.N;
         if (!shape_compiled(g.logN, R))
@@ -765,6 +769,25 @@ int cme_batch_info(cme_batch b, int* count, long* total_modes, int* precision, i
 }
 
 void* cme_batch_stream(cme_batch b) { return b ? (void*)b->stream : nullptr; }
+
+int cme_batch_plan(cme_batch b, int group, int* N, int* radix, int* inst_per_cta, int* cluster,
+                   int* persistent)
+{
+    if (!b || group < 0 || group >= (int)b->groups.size())
+        return fail(CME_ERR_INVALID_ARG, "cme_batch_plan: no group %d", group);
+    const auto& g = b->groups[group];
+    if (N)
+        *N = g.N;
+    if (radix)
+        *radix = g.large ? 8 : g.R;
+    if (inst_per_cta)
+        *inst_per_cta = g.large ? 1 : g.G;
+    if (cluster)
+        *cluster = g.C;
+    if (persistent)
+        *persistent = b->mode;
+    return CME_OK;
+}
 
 }  // extern "C"
 

@@ -87,7 +87,7 @@ def test_cluster_equals_one_block_bitwise(N, C, prec, integ):
     insts = random_set(N, 3300 + N, 3)
     out = {}
     for c in (1, C):
-        b = batch_of(insts, prec, integ, cluster=c)
+        b = batch_of(insts, prec, integ, radix=8, cluster=c)   # same values per thread
         b.step(1e-3, 37)
         b.synchronize()
         out[c] = b.get_state()
@@ -160,3 +160,21 @@ def test_cluster_adjoint_equals_one_block_bitwise(N, C, prec):
         for key in out[1]:
             e1, eC = rel(out[1][key], ref[key]), rel(out[C][key], ref[key])
             assert eC <= max(2 * e1, 1e-6), (key, e1, eC)
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_plans_run_the_kernels_the_tests_mean(prec):
+    """The cluster tests above do run clusters: an explicit cluster request without a radix
+    selects the clusters' 8 values per thread, also where the library would otherwise choose 16
+    (FP32, N >= 2048); and the library's own choice for few FP64 instances is a cluster."""
+    insts = random_set(4096, 3700, 2)
+    b = batch_of(insts, prec, cluster=4)
+    assert b.plan(0)["radix"] == 8 and b.plan(0)["cluster"] == 4
+    b.close()
+    b = batch_of(insts, prec)
+    p = b.plan(0)
+    if prec == cme.FP64:
+        assert p["cluster"] == 8 and p["radix"] == 8
+    else:
+        assert p["cluster"] == 1 and p["radix"] == 16
+    b.close()
