@@ -96,3 +96,24 @@ def test_large_and_small_in_one_batch():
     for g, inst in zip(b.split(b.get_state()), insts):
         r = fft_engine.rk4ip(fft_engine.Batch([inst]), 1e-3, 40)[0]
         assert rel(g, r) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_largest_sizes(prec):
+    """The top of the supported range: N = 2^20 (split 1024 x 1024) transform against
+    numpy.fft, and N = 2^19 (1024 x 512) RK4IP against the Eq. 4 engine."""
+    N = 1 << 20
+    inst = wl.random_instance(N, 2300, amp=0.3 * np.sqrt(64.0 / N))
+    b = batch_of([inst], prec)
+    got = b.transform(+1)
+    ref = np.fft.ifft(np.fft.ifftshift(inst.D0)) * N
+    tol = 1e-13 if prec == cme.FP64 else 2e-6
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)) * np.log2(N)
+    b.close()
+    N = 1 << 19
+    insts = [wl.make_instance(N, 1e-4, 0.0, 2.0, 2.0, 1e-4, seed=2310)]
+    b = batch_of(insts, prec)
+    b.step(1e-4, 10)
+    got = b.get_state()
+    ref = fft_engine.rk4ip(fft_engine.Batch(insts), 1e-4, 10)[0]
+    assert rel(got, ref) <= (1e-12 if prec == cme.FP64 else 1e-5)

@@ -301,7 +301,8 @@ def uneven_sample_indices():
 @pytest.mark.parametrize("persistent", [1, 2])
 def test_uneven_modes_agree_bitwise_and_with_oracle(persistent):
     """Mixed N (4..4096) in one batch: the persistent work-list kernel and the concurrent
-    per-group kernels give identical fields; both agree with the oracle."""
+    per-group kernels agree (FP64: to 1e-14 -- the per-group plan may run other values per
+    thread than the work-list tiles); both agree with the oracle."""
     sizes = (4, 8, 64, 64, 256, 512, 1024, 2048, 4096)
     insts = [wl.random_instance(N, 1500 + i, amp=0.2 * min(1.0, np.sqrt(64.0 / N)), sigma=1.0,
                                 A_in=1.3) for i, N in enumerate(sizes)]
