@@ -46,37 +46,49 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    c_int, c_long, c_double = ctypes.c_int, ctypes.c_long, ctypes.c_double
+    lib.oracle_fwm.argtypes = [c_int, c_int, c_int, dp, dp]
+    lib.oracle_rhs.argtypes = [c_int, c_int, c_int, c_double, c_double, c_double, c_double,
+                               dp, dp]
+    lib.oracle_integrate.argtypes = [c_int, c_int, c_int, c_int, dp, dp, c_double, c_double,
+                                     c_double, c_double, c_double, c_double, c_long, dp]
+    lib.oracle_integrate_eq1.argtypes = [c_int, c_int, dp, dp, c_double, c_double,
+                                         c_double, c_double, c_double, c_double,
+                                         c_double, c_long, dp]
+    lib.oracle_dft.argtypes = [c_int, c_int, dp, dp]
+    lib.oracle_invariants.argtypes = [c_int, c_int, dp, c_double, c_double, dp, dp]
+    lib.oracle_rk4ip_grad.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
+                                      c_double, c_double, c_double, c_long, dp, dp,
+                                      c_double, dp, dp, dp, dp, dp]
+    lib.oracle_rk4ip_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
+                                      c_double, c_double, c_double, c_long, dp, dp,
+                                      c_double, dp]
+    lib.oracle_fwm_vjp.argtypes = [c_int, c_int, c_int, dp, dp, dp]
+    for name in ("oracle_fwm", "oracle_rhs", "oracle_integrate", "oracle_integrate_eq1",
+                 "oracle_dft", "oracle_invariants", "oracle_rk4ip_grad",
+                 "oracle_rk4ip_loss", "oracle_fwm_vjp"):
+        getattr(lib, name).restype = c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            dp = ctypes.POINTER(ctypes.c_double)
-            c_int, c_long, c_double = ctypes.c_int, ctypes.c_long, ctypes.c_double
-            lib.oracle_fwm.argtypes = [c_int, c_int, c_int, dp, dp]
-            lib.oracle_rhs.argtypes = [c_int, c_int, c_int, c_double, c_double, c_double, c_double,
-                                       dp, dp]
-            lib.oracle_integrate.argtypes = [c_int, c_int, c_int, c_int, dp, dp, c_double, c_double,
-                                             c_double, c_double, c_double, c_double, c_long, dp]
-            lib.oracle_integrate_eq1.argtypes = [c_int, c_int, dp, dp, c_double, c_double,
-                                                 c_double, c_double, c_double, c_double,
-                                                 c_double, c_long, dp]
-            lib.oracle_dft.argtypes = [c_int, c_int, dp, dp]
-            lib.oracle_invariants.argtypes = [c_int, c_int, dp, c_double, c_double, dp, dp]
-            lib.oracle_rk4ip_grad.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
-                                              c_double, c_double, c_double, c_long, dp, dp,
-                                              c_double, dp, dp, dp, dp, dp]
-            lib.oracle_rk4ip_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
-                                              c_double, c_double, c_double, c_long, dp, dp,
-                                              c_double, dp]
-            lib.oracle_fwm_vjp.argtypes = [c_int, c_int, c_int, dp, dp, dp]
-            for name in ("oracle_fwm", "oracle_rhs", "oracle_integrate", "oracle_integrate_eq1",
-                         "oracle_dft", "oracle_invariants", "oracle_rk4ip_grad",
-                         "oracle_rk4ip_loss", "oracle_fwm_vjp"):
-                getattr(lib, name).restype = c_int
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def use_library(path: str) -> None:
+    """Route every oracle call of this process through the compiled oracle at `path` (a build
+    of a modified copy of cme_oracle.c: the test that plants mistakes in the oracle and checks
+    that its pins catch them)."""
+    global _lib
+    with _lock:
+        _lib = _configure(ctypes.CDLL(path))
 
 
 def _modes(inst) -> int:
