@@ -74,16 +74,17 @@ typedef struct cme_options {
                               kernel for all groups */
     int cluster;           /* thread blocks per instance (1, 2, 4 or 8) for N = 2048 and 4096
                               at 8 values per thread: C > 1 spreads each instance over a
-                              thread-block cluster whose blocks exchange through distributed
-                              shared memory (one kernel per N group; also used by cme_grad).
-                              With radix 0, a cluster request selects the clusters' 8
-                              values per thread.
-                              0 = library choice: FP64 batches take the largest C with
-                              instances * C <= SMs (FP64 arithmetic is the bound, so more
-                              SMs per instance pay); FP32 batches take C = 1 (their exchanges
-                              are latency bound, and a cluster exchange costs more than an
-                              in-block one).  Groups without a compiled cluster shape run
-                              C = 1. */
+                              thread-block cluster that runs a four-step transform (an
+                              N/C-point transform inside each block, one all-to-all through
+                              distributed shared memory, C-point transforms in registers;
+                              one kernel per N group; also used by cme_grad).  With radix 0,
+                              a cluster request selects the clusters' 8 values per thread.
+                              0 = library choice: the largest C with instances * C <= SMs,
+                              where C >= 4 in FP32 (FP32 steps are latency bound and a
+                              2-block cluster does not repay its all-to-all); FP32 gradients
+                              take the largest C with 2 * instances * C <= SMs, since their
+                              recomputation and backward kernels run side by side.  Groups
+                              without a compiled cluster shape run C = 1. */
 } cme_options;
 
 /* Fill *opt with the defaults: CME_FP64, CME_RK4IP, library-chosen launch shape, no graph. */

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                         z[j] = cconj(abar);                      // DFT(.) = conj(IDFT(conj .))
                     }
                 }
-                grp.inverse(z);
+                grp.inverse(z, p);
             }
             grp.mask(z);   // nor does F depend on them: the VJP of m F(m x), m the mask
             // z now holds conj(stage-input cotangent)

@@ -299,21 +299,28 @@ int plan_batch(cme_batch b, const cme_options& o)
             return fail(CME_ERR_INVALID_ARG, "launch plan: radix %d not available for N=%d", R, g.N);
         g.R = R;
         g.G = inst_per_block(g.N, R, o.inst_per_cta, g.count);
-        // blocks per instance: explicit, or (FP64 only) the largest cluster that still gives
-        // every instance's blocks their own SMs.  FP64 groups are bound by the FP64 pipes, so
-        // spreading an instance over C SMs pays (N = 4096 x 16: 437 -> 136 us per step); FP32
-        // groups are latency bound and each distributed-shared-memory exchange costs ~0.7 us,
-        // so they run one block per instance unless asked otherwise.
+        // blocks per instance: explicit, or the largest cluster that still gives every
+        // instance's blocks their own SMs.  FP64 groups are bound by the FP64 pipes (N = 4096
+        // x 16: 437 -> 123 us per step on 8-block clusters).  FP32 groups are latency bound;
+        // the four-step cluster transform costs one all-to-all (~0.5 us) per transform, which
+        // pays from 4 blocks on (N = 4096 x 16: 11.5 us per step on one block at 16 values
+        // per thread, 7.6 us on 8-block clusters), at the clusters' 8 values per thread.
         g.C = 1;
         if (o.cluster > 1) {
             if (cluster_shape_compiled(g.logN, R, o.cluster))
                 g.C = o.cluster;
-        } else if (o.cluster == 0 && b->prec == PREC_FP64 && (g.logN == 11 || g.logN == 12)) {
-            for (int c : {8, 4, 2})
-                if (cluster_shape_compiled(g.logN, R, c) && (long long)g.count * c <= b->sms) {
+        } else if (o.cluster == 0 && (g.logN == 11 || g.logN == 12)) {
+            const bool fp64 = b->prec == PREC_FP64;
+            for (int c : {8, 4, 2}) {
+                const int Rc = (fp64 || o.radix) ? R : 8;
+                if ((fp64 || c >= 4) && cluster_shape_compiled(g.logN, Rc, c) &&
+                    (long long)g.count * c <= b->sms) {
                     g.C = c;
+                    g.R = Rc;
+                    g.G = 1;
                     break;
                 }
+            }
         }
     }
     // library choice: one kernel per N group on concurrent streams (measured ahead of the
@@ -1627,13 +1634,30 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
     // Launch plan of the gradient's forward, recomputation and backward kernels, shared so
     // that the recomputation reproduces the forward states bit for bit.  FP32 takes 8 values
     // per thread: the backward kernel's live state spills at 16 (N = 4096: 47.3 against 50.4
-    // us per gradient step with the forward at 16).  FP64 keeps the batch's plan.
+    // us per gradient step with the forward at 16).  Unless the batch asked for a cluster
+    // size, FP32 groups of N = 2048, 4096 take the largest cluster for which the
+    // recomputation and the backward kernel, which run side by side, both get their own SMs
+    // (N = 4096 x 16: 47.2 us per gradient step on one block, 28.5 on 4-block clusters,
+    // 46.2 on 8-block clusters sharing SMs).  FP64 keeps the batch's plan.
     std::vector<LaunchGroup> ag(b->groups);
     for (auto& g : ag) {
         g.chunk = nullptr;   // copies never own the chunk graphs
-        if (b->prec == PREC_FP32 && g.C == 1) {
+        if (b->prec != PREC_FP32 || g.large)
+            continue;
+        if (b->opt.cluster == 0 && (g.logN == 11 || g.logN == 12)) {
+            g.C = 1;
+            for (int c : {8, 4})
+                if (cluster_shape_compiled(g.logN, 8, c) && 2LL * g.count * c <= b->sms) {
+                    g.C = c;
+                    break;
+                }
+        }
+        if (g.C == 1) {
             g.R = g.N <= 4 ? 4 : 8;
             g.G = inst_per_block(g.N, g.R, 0, g.count);
+        } else {
+            g.R = 8;
+            g.G = 1;
         }
     }
     // forward with checkpoints at the segment starts

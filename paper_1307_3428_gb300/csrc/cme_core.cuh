@@ -282,21 +282,12 @@ CME_DEV void group_sync()
 // ----------------------------------------------------------------------------------------
 // Transform of one group: x holds positions t + j*P; sign S (+1 inverse / time samples,
 // -1 forward).  tw holds exp(+2 pi i j k/(L r)) for the passes s >= 1.
-//
-// C > 1: the group's P threads are spread over the C blocks of a thread-block cluster, PC =
-// P/C threads each (thread t = rank PC + l).  Each block's exchange buffer holds the N/C
-// positions its own threads read, position t + jP at local index l + j PC (padded); a pass
-// stores each output straight into the buffer of the block that reads it next.
 // ----------------------------------------------------------------------------------------
-template <typename T, int LOGN, int R, bool WARP, int C = 1>
+template <typename T, int LOGN, int R, bool WARP>
 struct Transform {
     using PL = Plan<LOGN, R>;
     static constexpr int N = PL::N, P = PL::P, NS = PL::NS;
-    static_assert(C >= 1 && (C & (C - 1)) == 0 && P % C == 0, "cluster size");
-    static constexpr int PC = P / C;                 // threads per block of the cluster
-    static_assert(C == 1 || PC % 16 == 0, "padding identity needs PC % 16 == 0");
-    // elements per exchange buffer of one block
-    static constexpr int BUFC = C == 1 ? PL::BUF : N / C + N / C / 16 + 1;
+    static constexpr int BUF = PL::BUF;   // elements per exchange buffer
 
     template <int s, int S, class TW>
     CME_DEV static void pass(cx<T> (&x)[R], const TW& tw)
@@ -331,8 +322,6 @@ struct Transform {
         int rd;
         int wr[NS > 1 ? NS - 1 : 1];
         int wx0, wx1, rx0, rx1;   // XOR-layout bases of the stride-8 exchange (R = 8)
-        // C > 1: DSMEM address of every store of every exchange (buffer 0)
-        uint32_t wc[C > 1 && NS > 1 ? NS - 1 : 1][C > 1 ? R : 1];
     };
     // The exchange after a radix-8 pass of stride L = 8 uses the XOR layout
     // p -> p ^ (8 * bit6(p)) instead of the padding: its writes (p = 64 (t >> 3) + (t & 7) + 8j)
@@ -361,50 +350,13 @@ struct Transform {
         return a;
     }
 
-    // C > 1: thread t = rank PC + l; buf_saddr = shared address of this block's buffer 0.
-    // The store of output j of pass s goes to position p = (t - k) R + k + jL (k = t mod L),
-    // which is read by thread p mod P, i.e. by block (p mod P) / PC at local index
-    // (p mod PC) + (p / P) PC.
-    CME_DEV static Addr make_addr_cluster(int t, int l, uint32_t buf_saddr)
-    {
-        Addr a{};
-        a.rd = PL::pad(l);
-        if constexpr (C > 1) {
-#pragma unroll
-            for (int s = 0; s + 1 < NS; ++s) {
-                const int L = PL::L(s);
-                const int k = t & (L - 1);
-                const int b = (t - k) * R + k;
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const int p = b + j * L;
-                    const int q = p & (P - 1);
-                    const int loc = (q & (PC - 1)) + (p / P) * PC;
-                    a.wc[s][j] = dsmem_map(buf_saddr + 8u * (uint32_t)PL::pad(loc), q / PC);
-                }
-            }
-        }
-        return a;
-    }
-
     template <int s>
     CME_DEV static void exchange(cx<T> (&x)[R], const Xbuf<T>& b, const Addr& ad, int par)
     {
         static_assert(PL::radix(s) == R, "exchanges follow full-radix passes");
         constexpr int L = PL::L(s);
-        if constexpr (C > 1) {
-            // buffer `par` of the reading block: par * BUFC elements of W 8-byte words further
-            const uint32_t po = (uint32_t)par * (uint32_t)(BUFC * 8 * Xbuf<T>::words_per_elem);
-            const Xbuf<T> mine = b.at(par * BUFC);
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                mine.put_remote(ad.wc[s][j] + po, x[j]);
-            cluster_sync();
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                x[j] = mine.get(ad.rd + j * PC + ((j * PC) >> 4));
-        } else if constexpr (xor8(s)) {
-            const Xbuf<T> mine = b.at(par * BUFC);
+        const Xbuf<T> mine = b.at(par * BUF);
+        if constexpr (xor8(s)) {
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 mine.put(((j & 1) ? ad.wx1 : ad.wx0) + 8 * j, x[j]);
@@ -413,7 +365,6 @@ struct Transform {
             for (int j = 0; j < R; ++j)
                 x[j] = mine.get((((j * P) >> 6) & 1 ? ad.rx1 : ad.rx0) + j * P);
         } else {
-            const Xbuf<T> mine = b.at(par * BUFC);
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 mine.put(ad.wr[s] + j * L + ((j * L) >> 4), x[j]);
@@ -444,18 +395,64 @@ struct Transform {
     {
         run_from<0, S, TW>(x, tw, buf, par, ad);
     }
+};
 
+// ----------------------------------------------------------------------------------------
+// Four-step transform of one instance spread over the C blocks of a thread-block cluster
+// (N = C N2, P = N/R threads in all, PC = P/C per block; C divides R, G = R/C).
+//
+// With k = k1 + C k2 (k1 < C, k2 < N2) and n = n2 + N2 n1 (n2 < N2, n1 < C),
+//   a_n = sum_k1 exp(2 pi i n1 k1 / C) exp(2 pi i n2 k1 / N) sum_k2 X_k exp(2 pi i n2 k2 / N2),
+// so the inverse transform is an N2-point transform inside each block (block r holds k1 = r),
+// a twiddle, one all-to-all between the blocks, and C-point transforms in registers.
+//   Modes: thread l of block r holds k = r + C (l + PC j) = t + jP with t = r + C l.
+//   Time samples: the same thread holds n = t' + jP with t' = r PC + l.
+// Both layouts have the form t + jP, so the pointwise work (Kerr term, pump, Runge-Kutta
+// algebra, loads and stores) is unchanged; only which thread holds which mode differs.  The
+// transform from time samples back to modes runs the same stages in reverse order (the
+// forward transform is conj(inverse(conj .)) as for one block).
+//
+// One all-to-all moves every value once: each thread stores its R values into C blocks'
+// buffers with consecutive threads writing consecutive words, then one cluster barrier
+// (release/acquire) makes them visible.  Two ping-pong buffers per block: a buffer is
+// written again only two barriers after it was last read.
+// ----------------------------------------------------------------------------------------
+template <typename T, int LOGN, int R, int C>
+struct ClusterFFT {
+    static constexpr int LC = ilog2(C);
+    static_assert((1 << LC) == C && C >= 2 && C <= R && R % C == 0, "C divides R");
+    static constexpr int N = 1 << LOGN, P = N / R, PC = P / C, N2 = N / C, G = R / C;
+    static constexpr bool WARP = PC <= 32;
+    using TL = Transform<T, LOGN - LC, R, WARP>;     // the N2-point transform of one block
+    static_assert(TL::P == PC, "block threads");
+
+    // In-register C-point inverse transforms over slots {c G + m : c < C}, m < G.
+    CME_DEV static void radix_c(cx<T> (&x)[R])
+    {
+#pragma unroll
+        for (int m = 0; m < G; ++m) {
+            cx<T> v[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                v[c] = x[c * G + m];
+            dft<C, +1>(v);
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                x[c * G + m] = v[c];
+        }
+    }
 };
 
 // Twiddles exp(2 pi i j k / (L r)) of pass s >= 1 for butterfly q of thread t, where
 // k = (t + qP) mod L, taken from the table exp(2 pi i m / N).  IN_REGS = true loads all of
 // them into registers once per launch; otherwise each pass reads them from the table through
 // the read-only cache (large N, where registers are scarce).
-template <typename T, int LOGN, int R, bool IN_REGS>
+// TS: the table holds exp(2 pi i m / (TS N)) (a larger transform's table, read at stride TS).
+template <typename T, int LOGN, int R, bool IN_REGS, int TS = 1>
 struct Twiddles;
 
-template <typename T, int LOGN, int R>
-struct Twiddles<T, LOGN, R, true> {
+template <typename T, int LOGN, int R, int TS>
+struct Twiddles<T, LOGN, R, true, TS> {
     using PL = Plan<LOGN, R>;
     cx<T> w[PL::NTW > 0 ? PL::NTW : 1];
 
@@ -471,7 +468,7 @@ struct Twiddles<T, LOGN, R, true> {
 #pragma unroll
                 for (int j = 1; j < r; ++j)
                     w[(s - 1) * (R - 1) + q * (r - 1) + (j - 1)] =
-                        gload<T>(table, (j * k * stride) & (PL::N - 1));
+                        gload<T>(table, ((j * k * stride) & (PL::N - 1)) * TS);
             }
             init_from<s + 1>(table, t);
         }
@@ -489,8 +486,8 @@ struct Twiddles<T, LOGN, R, true> {
     }
 };
 
-template <typename T, int LOGN, int R>
-struct Twiddles<T, LOGN, R, false> {
+template <typename T, int LOGN, int R, int TS>
+struct Twiddles<T, LOGN, R, false, TS> {
     using PL = Plan<LOGN, R>;
     const cx<T>* table;
     int kst[PL::NS > 1 ? PL::NS : 1];  // (t mod L_s) * N / (L_s r_s) per pass
@@ -509,7 +506,7 @@ struct Twiddles<T, LOGN, R, false> {
     {
         // butterfly q > 0 only occurs in the last pass, where k = t + qP exactly
         constexpr int r = PL::radix(s), L = PL::L(s), stride = PL::N / (L * r);
-        return gload<T>(table, (j * kst[s] + j * q * PL::P * stride) & (PL::N - 1));
+        return gload<T>(table, ((j * kst[s] + j * q * PL::P * stride) & (PL::N - 1)) * TS);
     }
 };
 
@@ -517,7 +514,7 @@ struct Twiddles<T, LOGN, R, false> {
 // array [(pass, butterfly, j)][P] (no bank conflicts; no thread reads another's slot, so no
 // barrier is needed after the fill).  Used where registers are too scarce and the table loads
 // would crowd the global-load queue (FP32, N >= 2048).
-template <typename T, int LOGN, int R>
+template <typename T, int LOGN, int R, int TS = 1>
 struct TwiddlesSmem {
     using PL = Plan<LOGN, R>;
     const cx<T>* base;   // this thread's slot 0
@@ -539,7 +536,7 @@ struct TwiddlesSmem {
 #pragma unroll
                 for (int j = 1; j < r; ++j)
                     smem_tw[((s - 1) * (R - 1) + q * (r - 1) + (j - 1)) * PL::P + t] =
-                        gload<T>(table, (j * k * stride) & (PL::N - 1));
+                        gload<T>(table, ((j * k * stride) & (PL::N - 1)) * TS);
             }
             init_from<s + 1>(table, t, smem_tw);
         }

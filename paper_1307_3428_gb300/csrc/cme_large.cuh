@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
     for (int j = 0; j < R; ++j)
         x[j] = yrow[j * P];
     if (A.diag == LDIAG_IDFT) {
-        grp.inverse(x);
+        grp.inverse(x, 0);
         if (valid) {
             cx<T>* d = reinterpret_cast<cx<T>*>(A.diag_out) + A.base + ibase + j1;
 #pragma unroll
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
             const cx<T> v = z[j * estride];
             x[j] = {v.re, -v.im};
         }
-        grp.inverse(x);
+        grp.inverse(x, 1);
 #pragma unroll
         for (int j = 0; j < R; ++j)
             x[j].im = -x[j].im;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     if (st == LARGE_FINAL)
         return;
     // inverse transform over m1 of the next stage input, twiddle, store Y column m2
-    grp.inverse(x);
+    grp.inverse(x, 0);
     if (valid) {
         cx<T>* y = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)t * N2 + m2;
 #pragma unroll

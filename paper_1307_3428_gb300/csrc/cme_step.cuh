@@ -70,6 +70,19 @@ struct Props {
 template <typename T, int LOGN>
 constexpr bool twiddles_in_regs() { return sizeof(T) == 4 ? LOGN <= 10 : LOGN <= 9; }
 
+// The transform of a group: one block's Stockham transform, or for C > 1 the four-step
+// cluster transform and its transform inside one block.
+template <typename T, int LOGN, int R, int C>
+struct GroupFFT {
+    using CF = ClusterFFT<T, LOGN, R, C>;
+    using TF = typename CF::TL;
+};
+template <typename T, int LOGN, int R>
+struct GroupFFT<T, LOGN, R, 1> {
+    using CF = void;
+    using TF = Transform<T, LOGN, R, (Plan<LOGN, R>::P <= 32)>;
+};
+
 // Per-thread view of one instance: the transform machinery plus the instance constants.
 // C > 1: the instance is spread over the C blocks of a thread-block cluster.
 template <typename T, int LOGN, int R, int C = 1>
@@ -78,19 +91,34 @@ struct Group {
     static constexpr int N = PL::N, P = PL::P;
     static constexpr bool WARP = (C == 1 && P <= 32);
     static constexpr bool COMP = (sizeof(T) == 4);  // compensated state in FP32
-    using TF = Transform<T, LOGN, R, WARP, C>;
+    // C > 1: the four-step cluster transform; TF is then its transform inside one block
+    using CF = typename GroupFFT<T, LOGN, R, C>::CF;
+    using TF = typename GroupFFT<T, LOGN, R, C>::TF;
+    static constexpr int LC = ilog2(C);
     // twiddles: registers (small N), this group's shared memory (FP32 one-block groups of
-    // N >= 2048), else the global table
-    static constexpr bool TW_SMEM = C == 1 && !twiddles_in_regs<T, LOGN>() &&
-                                    twiddles_in_smem(sizeof(T), LOGN);
-    using TW = std::conditional_t<TW_SMEM, TwiddlesSmem<T, LOGN, R>,
-                                  Twiddles<T, LOGN, R, twiddles_in_regs<T, LOGN>()>>;
+    // N >= 2048), else the global table (read at stride C by the block transforms of a cluster)
+    static constexpr bool TW_REGS =
+        twiddles_in_regs<T, LOGN - LC>() && (C == 1 || sizeof(T) == 4);
+    static constexpr bool TW_SMEM = !TW_REGS && twiddles_in_smem(sizeof(T), LOGN - LC);
+    using TW = std::conditional_t<TW_SMEM, TwiddlesSmem<T, LOGN - LC, R, C>,
+                                  Twiddles<T, LOGN - LC, R, TW_REGS, C>>;
 
-    int t;
+    int t;         // the thread holds modes t + jP
     int par;
     Xbuf<T> buf;   // first of the two ping-pong exchange buffers
     typename TF::Addr ad;
     TW tw;
+
+    // C > 1: all-to-all state (block `rank`, thread l): this thread's slots of the receive
+    // buffer 0; shared::cluster address of receive buffer 0 in every block; byte offsets of
+    // this thread's stores; the twiddles of the two directions in this block's shared memory
+    // (thread-major); the receive-buffer parity.
+    Xbuf<T> abuf;
+    uint32_t rb[C > 1 ? C : 1];
+    uint32_t om, ot;
+    const cx<T>* twm;
+    const cx<T>* twt;
+    int apar;
     // Physical modes (the zero padding of Sec. 2): of the N modes only the centred M,
     // mu = mlo .. mhi, are physical; the right-hand side is zero on the others, which stay at
     // zero.  masked = false (M = N) skips the test.
@@ -123,8 +151,56 @@ struct Group {
     }
 
     // The step loops contain a single copy of the transform code (instruction-cache
-    // footprint): the forward transform is computed as conj(inverse(conj(x))).
-    CME_DEV void inverse(cx<T> (&x)[R]) { TF::template run<+1>(x, tw, buf, par, ad); }
+    // footprint): the forward transform is computed as conj(inverse(conj(x))).  d = 0 takes
+    // modes to time samples, d = 1 time samples to modes (the same for one block; the
+    // reverse order of the stages for a cluster).
+    CME_DEV void inverse(cx<T> (&x)[R], int d)
+    {
+        if constexpr (C == 1) {
+            TF::template run<+1>(x, tw, buf, par, ad);
+        } else {
+            if (d == 1) {
+                CF::radix_c(x);
+                twiddle(x, twt);
+                all_to_all<true>(x);
+            }
+            TF::template run<+1>(x, tw, buf, par, ad);
+            if (d == 0) {
+                twiddle(x, twm);
+                all_to_all<false>(x);
+                CF::radix_c(x);
+            }
+        }
+    }
+    CME_DEV static void twiddle(cx<T> (&x)[R], const cx<T>* w)
+    {
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            x[j] = cmul(x[j], w[j * CF::PC]);
+    }
+    // Cluster all-to-all.  Modes to time (T2M = false): the value of local position
+    // n2 = l + PC j (k1 = rank) goes to block j mod C, slot rank G + j / C.  Time to modes:
+    // slot i = k1 G + m of thread (rank, l) goes to block k1, slot rank + C m.  Every thread
+    // reads its slots j at l + PC j of its own buffer.
+    template <bool T2M>
+    CME_DEV void all_to_all(cx<T> (&x)[R])
+    {
+        constexpr int PC = CF::PC, G = CF::G;
+        const uint32_t po = (uint32_t)apar * (uint32_t)(CF::N2 * 8 * Xbuf<T>::words_per_elem);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if constexpr (T2M)
+                abuf.put_remote(rb[j / G] + ot + po + (uint32_t)(8 * PC * C * (j % G)), x[j]);
+            else
+                abuf.put_remote(rb[j % C] + om + po + (uint32_t)(8 * PC * (j / C)), x[j]);
+        }
+        cluster_sync();
+        const Xbuf<T> mine = abuf.at(apar * CF::N2);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            x[j] = mine.get(PC * j);
+        apar ^= 1;
+    }
 
     // F(x) = pump + i (g0/N) DFT(|a|^2 a), a = inverse transform of x   (Eq. 4)
     CME_DEV void rhs(cx<T> (&x)[R], T gN, cx<T> pump) { rhs_store_a(x, gN, pump, nullptr); }
@@ -134,7 +210,7 @@ struct Group {
     {
 #pragma unroll 1
         for (int d = 0; d < 2; ++d) {
-            inverse(x);
+            inverse(x, d);
             if (d == 0 && aout) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
@@ -189,23 +265,53 @@ struct Group {
         set_modes(N);
     }
 
-    // Cluster set-up (C > 1): block `rank` of the cluster, thread l of the block; the block's
-    // dynamic shared memory holds its two exchange buffers.
+    // Cluster set-up (C > 1): block `rank` of the cluster, thread l of the block.  The block's
+    // dynamic shared memory holds the two exchange buffers of its N2-point transform, the two
+    // all-to-all receive buffers, the two twiddle arrays of the four-step transform and (FP32,
+    // N2 >= 2048) the pass twiddles of the N2-point transform.
     CME_DEV void setup_cluster(unsigned char* smem, int rank, int l, const void* tw_table)
     {
         static_assert(C > 1, "cluster groups only");
+        constexpr int W = Xbuf<T>::words_per_elem, PC = CF::PC, N2 = CF::N2, G = CF::G;
+        unsigned char* a2a = smem + (size_t)2 * TF::BUF * 8 * W;
+        cx<T>* tws = reinterpret_cast<cx<T>*>(a2a + (size_t)2 * N2 * 8 * W);
         if constexpr (sizeof(T) == 4) {
             buf.p = reinterpret_cast<float2*>(smem);
+            abuf.p = reinterpret_cast<float2*>(a2a) + l;
         } else {
             buf.re = reinterpret_cast<double*>(smem);
-            buf.stride = TF::BUFC;
+            buf.stride = TF::BUF;
+            abuf.re = reinterpret_cast<double*>(a2a) + l;
+            abuf.stride = N2;
         }
         accS = nullptr;
         accL = nullptr;
-        t = rank * TF::PC + l;
+        t = rank + C * l;
         par = 0;
-        ad = TF::make_addr_cluster(t, l, smem_addr(smem));
-        tw.init(tw_table, t);
+        apar = 0;
+        ad = TF::make_addr(l);
+        if constexpr (TW_SMEM)
+            tw.init(tw_table, l, tws + 2 * N2);
+        else
+            tw.init(tw_table, l);
+        const uint32_t a0 = smem_addr(a2a);
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            rb[c] = dsmem_map(a0, c);
+        om = 8u * (uint32_t)(l + PC * rank * G);
+        ot = 8u * (uint32_t)(l + PC * rank);
+        // exp(2 pi i n2 k1 / N): after the block transform (n2 = l + PC j, k1 = rank), and
+        // after the C-point transforms (n2 = rank PC + l + P (i mod G), k1 = i / G)
+        const int tp = rank * PC + l;
+        cx<T>* wm = tws + l;
+        cx<T>* wt = tws + N2 + l;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            wm[j * PC] = gload<T>(tw_table, ((l + PC * j) * rank) & (N - 1));
+            wt[j * PC] = gload<T>(tw_table, ((tp + P * (j % G)) * (j / G)) & (N - 1));
+        }
+        twm = wm;
+        twt = wt;
         set_modes(N);
     }
 };
@@ -214,7 +320,11 @@ struct Group {
 template <typename T, int LOGN, int R, int C>
 constexpr size_t cluster_smem_bytes()
 {
-    return (size_t)2 * Transform<T, LOGN, R, false, C>::BUFC * 8 * Xbuf<T>::words_per_elem;
+    using CF = ClusterFFT<T, LOGN, R, C>;
+    constexpr size_t W = Xbuf<T>::words_per_elem;
+    return (size_t)2 * CF::TL::BUF * 8 * W + (size_t)2 * CF::N2 * 8 * W +
+           (size_t)2 * CF::N2 * sizeof(cx<T>) +
+           (Group<T, LOGN, R, C>::TW_SMEM ? tw_bytes(sizeof(T), LOGN - CF::LC, R) : 0);
 }
 
 template <typename T>
@@ -431,7 +541,7 @@ CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
                 x[j] = fs.Dh[j];
 #pragma unroll 1
             for (int d = 0; d < 2; ++d) {
-                grp.inverse(x);
+                grp.inverse(x, d);
                 if (d == 0) {
 #pragma unroll
                     for (int j = 0; j < R; ++j) {

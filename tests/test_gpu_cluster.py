@@ -1,14 +1,12 @@
 """Instances spread over a thread-block cluster (cme_options.cluster = C > 1): the C blocks hold
-P/C threads each and exchange through distributed shared memory.
+P/C threads each and run a four-step transform, an N/C-point transform inside each block and
+C-point transforms in registers, with one all-to-all through distributed shared memory per
+transform.
 
-The cluster kernels do the same arithmetic as the one-block kernels, in the same order; only
-where a value waits between two passes differs.  So besides the oracle comparisons (N = 256
-with C = 2 against the direct-sum oracle, N = 2048 and 4096 against the oracle's Eq. 4 engine,
-the adjoint at N = 256 against the oracle's adjoint), the cluster results equal the one-block
-results bit for bit wherever both hold the propagators the same way: always in FP64, and in
-FP32 up to N = 1024.  FP32 cluster kernels for N >= 2048 keep the propagators in registers
-(their blocks are small enough) where the one-block kernel reads them from memory; the
-compiler may then fuse a multiply-add differently, so there the two agree to FP32 rounding."""
+Checked against the oracle (N = 256 with C = 2 against the direct-sum oracle, N = 2048 and
+4096 against the oracle's Eq. 4 engine, the adjoint at N = 256 against the oracle's adjoint),
+and against the one-block kernels, which round in another order: the two agree to the
+precision's rounding."""
 import numpy as np
 import pytest
 
@@ -34,10 +32,6 @@ def rel(x, y):
 def batch_of(insts, prec, integ=cme.RK4IP, **kw):
     return cme.Batch([cme.Instance.from_workload(i) for i in insts], precision=prec,
                      integrator=integ, **kw)
-
-
-def same_policies(N, prec):
-    return prec == cme.FP64 or N <= 1024
 
 
 def random_set(N, seed, count):
@@ -83,7 +77,7 @@ def test_cluster_rk4ip_matches_eq4_engine(N, C, prec):
 @pytest.mark.parametrize("integ", [cme.RK4IP, cme.STRANG])
 @pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
 @pytest.mark.parametrize("N,C", [(256, 2), (2048, 4), (4096, 2), (4096, 8)])
-def test_cluster_equals_one_block_bitwise(N, C, prec, integ):
+def test_cluster_agrees_with_one_block(N, C, prec, integ):
     insts = random_set(N, 3300 + N, 3)
     out = {}
     for c in (1, C):
@@ -92,10 +86,7 @@ def test_cluster_equals_one_block_bitwise(N, C, prec, integ):
         b.synchronize()
         out[c] = b.get_state()
         b.close()
-    if same_policies(N, prec):
-        assert np.array_equal(out[1], out[C])
-    else:
-        assert rel(out[C], out[1]) <= 1e-6
+    assert rel(out[C], out[1]) <= (1e-12 if prec == cme.FP64 else 1e-5)
 
 
 def test_cluster_inside_a_mixed_batch():
@@ -137,11 +128,11 @@ def test_cluster_adjoint_n256_matches_oracle_adjoint():
 
 @pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
 @pytest.mark.parametrize("N,C", [(256, 2), (4096, 8)])
-def test_cluster_adjoint_equals_one_block_bitwise(N, C, prec):
-    """Where the policies differ (FP32, N = 4096) the comparison is against the FP64 gradient:
-    parameter gradients are sums over modes that cancel, which FP32 determines only loosely
-    (tenths of a percent here), so the cluster FP32 gradient must be as close to FP64 as the
-    one-block FP32 gradient is."""
+def test_cluster_adjoint_agrees_with_one_block(N, C, prec):
+    """Against the one-block FP64 gradient.  In FP64 the cluster gradient agrees with it to
+    rounding.  Parameter gradients are sums over modes that cancel, which FP32 determines only
+    loosely, so the cluster FP32 gradient must be about as close to FP64 as the one-block FP32
+    gradient is: within 4 times its error (the two round in different orders), or 1e-5."""
     insts = [wl.make_instance(N, 0.01, 1e-4, 2.0 + k, 2.0, 1e-3, seed=3600 + k) for k in range(2)]
     T = np.concatenate([target_for(N, 3610 + k) for k in range(2)])
 
@@ -151,30 +142,38 @@ def test_cluster_adjoint_equals_one_block_bitwise(N, C, prec):
         b.close()
         return g
 
-    out = {c: grad(prec, c) for c in (1, C)}
-    if same_policies(N, prec):
-        for key in out[1]:
-            assert np.array_equal(out[1][key], out[C][key]), key
+    ref = grad(cme.FP64, 1)
+    got = grad(prec, C)
+    if prec == cme.FP64:
+        for key in ref:
+            assert rel(got[key], ref[key]) <= 1e-9, key
     else:
-        ref = grad(cme.FP64, C)
-        for key in out[1]:
-            e1, eC = rel(out[1][key], ref[key]), rel(out[C][key], ref[key])
-            assert eC <= max(2 * e1, 1e-6), (key, e1, eC)
+        one = grad(prec, 1)
+        for key in ref:
+            e1, eC = rel(one[key], ref[key]), rel(got[key], ref[key])
+            assert eC <= max(4 * e1, 1e-5), (key, e1, eC)
 
 
 @pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
 def test_plans_run_the_kernels_the_tests_mean(prec):
     """The cluster tests above do run clusters: an explicit cluster request without a radix
     selects the clusters' 8 values per thread, also where the library would otherwise choose 16
-    (FP32, N >= 2048); and the library's own choice for few FP64 instances is a cluster."""
+    (FP32, N >= 2048).  The library's own choice for few instances of N = 4096 is an 8-block
+    cluster; with more instances than SMs / 4, FP32 keeps one block per instance (16 values per
+    thread), while FP64 takes the largest cluster that fits."""
     insts = random_set(4096, 3700, 2)
     b = batch_of(insts, prec, cluster=4)
     assert b.plan(0)["radix"] == 8 and b.plan(0)["cluster"] == 4
     b.close()
     b = batch_of(insts, prec)
     p = b.plan(0)
+    assert p["cluster"] == 8 and p["radix"] == 8
+    b.close()
+    many = [insts[k % 2] for k in range(64)]
+    b = batch_of(many, prec)
+    p = b.plan(0)
     if prec == cme.FP64:
-        assert p["cluster"] == 8 and p["radix"] == 8
+        assert p["cluster"] == 2 and p["radix"] == 8
     else:
         assert p["cluster"] == 1 and p["radix"] == 16
     b.close()
