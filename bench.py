@@ -230,25 +230,40 @@ def run_adjoint(args, world, rank, local):
     D0 = np.concatenate([i.D0 for i in w.instances])
     d0 = torch.from_numpy(D0.view(np.float64).copy()).cuda()
 
-    def timed(prec, n, reps):
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def timed(prec, n, reps, warmup, sampler=None):
+        """Mean device time of `reps` gradients (CUDA events on the batch's stream, L2 flushed
+        before each), after `warmup` untimed ones (the first allocates the scratch)."""
         b = cme.Batch(insts, precision=prec, cluster=args.cluster)
-        b.set_state_device(d0.data_ptr())
-        b.grad(w.h, n, T)                      # warm-up (allocates the scratch)
-        ts = []
-        for _ in range(reps):
+        stream = torch.cuda.ExternalStream(b.stream)
+        for _ in range(warmup):
             b.set_state_device(d0.data_ptr())
+            b.grad(w.h, n, T)
+        ts = []
+        if sampler:
+            sampler.start()
+        for _ in range(reps):
+            flush.zero_()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.set_state_device(d0.data_ptr())
             g = b.grad(w.h, n, T)              # synchronises
-            ts.append(time.perf_counter() - t0)
-        return min(ts), g
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        clocks = sampler.stop() if sampler else None
+        b.close()
+        return sum(ts) / len(ts), g, clocks
 
     launches0 = cme.kernel_launches()
-    t32, g32 = timed(cme.FP32, nsteps, args.steps)
-    launches = (cme.kernel_launches() - launches0) // (args.steps + 1)
+    t32, g32, clocks = timed(cme.FP32, nsteps, args.steps, args.warmup, ClockSampler(local))
+    launches = (cme.kernel_launches() - launches0) // (args.steps + args.warmup)
     n64 = min(nsteps, 1000)
-    t64, g64 = timed(cme.FP64, n64, 1)
-    _, g32s = timed(cme.FP32, n64, 1)
+    t64, g64, _ = timed(cme.FP64, n64, 1, 1)
+    _, g32s, _ = timed(cme.FP32, n64, 1, 1)
     mode_steps = N * B * nsteps
     # forward, recomputation and backward: three times the forward step's 8 transforms of
     # 5 N log2 N flop plus ~80 pointwise flop per mode
@@ -260,11 +275,14 @@ def run_adjoint(args, world, rank, local):
     line = {
         "metric": "gradient mode-steps/s (forward + discrete adjoint), log-spectrum loss",
         "value": mode_steps / t32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": 1, "ms_per_step": t32 * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": t32 * 1e3, "higher_is_better": True,
+        "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"adjoint_n4096_b16: N=4096 x 16, {nsteps} RK4IP steps of "
                                "h=2e-4, sqrt(n) checkpoints, sech^2 log-spectrum targets",
-                   "cluster": args.cluster or "library choice"},
+                   "cluster": args.cluster or "library choice",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "basis": "3 x (8 transforms of 5 N log2 N + 80) flop per mode-step: forward, "

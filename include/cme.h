@@ -171,7 +171,8 @@ int cme_step(cme_batch b, double h, long nsteps);
  * NULL) receives it.  Synchronises.  Errors: INVALID_ARG, CUDA. */
 int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out);
 
-/* Wait for the batch's stream; returns CME_ERR_NONFINITE if any instance's status is set. */
+/* Wait for the batch's stream; returns CME_ERR_TIMEOUT if any instance's status is 2, else
+ * CME_ERR_NONFINITE if any instance's status is set. */
 int cme_synchronize(cme_batch b);
 
 /* Copy out one instance (idx >= 0) or all instances concatenated (idx = -1) to host memory:
@@ -196,8 +197,17 @@ int cme_get_time(cme_batch b, double* tau);
 int cme_set_time(cme_batch b, double tau);
 
 /* Per-instance status words (host array of `count` ints): 0 = finite, 1 = non-finite value
- * seen at the end of a launch.  Synchronises. */
+ * seen at the end of a launch, 2 = a bounded wait of a cluster all-to-all gave up (the
+ * instance's results are not valid).  Synchronises. */
 int cme_status(cme_batch b, int* per_instance);
+
+/* Test of the failure path of the bounded device waits (not for normal use): what = 1 makes
+ * the cluster all-to-alls of later cme_step / cme_grad calls expect 8 bytes more than are
+ * sent and poll only briefly, so their waits run out; the instances then report status 2 and
+ * cme_synchronize / cme_grad return CME_ERR_TIMEOUT, with no device fault.  what = 0 restores
+ * normal operation (cme_set_state clears the status words).  Batches without use_graph only.
+ * Errors: INVALID_ARG. */
+int cme_debug_fault(cme_batch b, int what);
 
 /* ---- gradients (discrete adjoint) ------------------------------------------------------- */
 
@@ -224,7 +234,8 @@ typedef struct cme_grads {
  * current one, on a second stream).  The batch ends at the final field (tau advanced by
  * h nsteps).  Scratch memory -- ceil(nsteps/segment) checkpoints and the states plus stage
  * values of two segments, 8 * segment field vectors -- is allocated on the first call and kept
- * with the batch.  RK4IP batches only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM. */
+ * with the batch.  RK4IP batches only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM,
+ * TIMEOUT (a bounded wait of a cluster all-to-all gave up). */
 int cme_grad(cme_batch b, double h, long nsteps, const double* target, double eps, long segment,
              cme_grads* out);
 

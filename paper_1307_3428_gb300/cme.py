@@ -87,6 +87,7 @@ _SIGS = [
     ("cme_get_time", ctypes.c_int, [_VP, _DP]),
     ("cme_set_time", ctypes.c_int, [_VP, ctypes.c_double]),
     ("cme_status", ctypes.c_int, [_VP, _IP]),
+    ("cme_debug_fault", ctypes.c_int, [_VP, ctypes.c_int]),
     ("cme_grad", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long, _DP, ctypes.c_double,
                                 ctypes.c_long, ctypes.POINTER(Grads)]),
     ("cme_rk4ip_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -310,6 +311,11 @@ class Batch:
         out = np.zeros(self.count, dtype=np.int32)
         _check(load().cme_status(self.handle, out.ctypes.data_as(_IP)))
         return out
+
+    def debug_fault(self, what: int):
+        """Test of the bounded device waits (cme_debug_fault): 1 makes later cluster
+        all-to-alls run out their waits, 0 restores normal operation."""
+        _check(load().cme_debug_fault(self.handle, int(what)))
 
     def checkpoint(self) -> bytes:
         n = ctypes.c_size_t()

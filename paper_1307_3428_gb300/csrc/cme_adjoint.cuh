@@ -85,7 +85,7 @@ CME_DEV int adj_setup(Group<T, LOGN, R, C>& grp, unsigned char* smem, const Step
         grp.setup(smem, g, threadIdx.x - g * P, a.tw);
     } else {
         inst = blockIdx.x / C;
-        grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw);
+        grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw, a.a2a_fault);
     }
     if (a.phys)
         grp.set_modes(a.phys[inst]);
@@ -120,8 +120,10 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
     fs.load(reinterpret_cast<const cx<T>*>(A.ckpt_hi) + s * TT + off + t,
             reinterpret_cast<const cx<T>*>(A.ckpt_lo) + s * TT + off + t);
     // this thread's slots of step 0 of the segment (surplus groups of a packed block recompute
-    // the last instance for the barriers and store nothing)
-    cx<T>* out = reinterpret_cast<cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + t;
+    // the last instance for the barriers and store nothing); the stage buffer is private to
+    // the two roles, so it is indexed by the coalesced scratch slot ts
+    cx<T>* out =
+        reinterpret_cast<cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + grp.ts;
     if constexpr (C > 1)
         cluster_sync();   // every block of the cluster runs before the first remote store
     for (long long i = 0; i < ns; ++i) {
@@ -133,6 +135,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
         }
         rk4ip_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
     }
+    if (grp.failed() && a.status)
+        a.status[inst] = 2;
     if constexpr (C > 1)
         cluster_sync();   // no block leaves while a peer may still address its shared memory
 }
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
     const long long TT = A.total, s = A.seg;
     const long long ns = (A.nsteps - s * A.K < A.K) ? A.nsteps - s * A.K : A.K;
     const cx<T>* buf =
-        reinterpret_cast<const cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + t;
+        reinterpret_cast<const cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + grp.ts;
     cx<T>* dbp = reinterpret_cast<cx<T>*>(A.dbar) + off + t;
     double2* glp = A.gL + off + t;
 
@@ -272,6 +276,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
         if (t == 0)
             A.pbar[inst] = pb;
     }
+    if (grp.failed() && a.status)
+        a.status[inst] = 2;
     if constexpr (C > 1)
         cluster_sync();   // no block leaves while a peer may still address its shared memory
 }

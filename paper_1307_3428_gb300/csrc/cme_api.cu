@@ -164,6 +164,7 @@ constexpr int LARGE_CHUNK = 32;
 }  // namespace
 
 struct cme_batch_s {
+    int a2a_fault = 0;   // cme_debug_fault
     int count = 0;
     long long total = 0;
     cme_options opt{};
@@ -299,26 +300,40 @@ int plan_batch(cme_batch b, const cme_options& o)
             return fail(CME_ERR_INVALID_ARG, "launch plan: radix %d not available for N=%d", R, g.N);
         g.R = R;
         g.G = inst_per_block(g.N, R, o.inst_per_cta, g.count);
-        // blocks per instance: explicit, or the largest cluster that still gives every
-        // instance's blocks their own SMs.  FP64 groups are bound by the FP64 pipes (N = 4096
-        // x 16: 437 -> 123 us per step on 8-block clusters).  FP32 groups are latency bound;
-        // the four-step cluster transform costs one all-to-all (~0.5 us) per transform, which
-        // pays from 4 blocks on (N = 4096 x 16: 11.5 us per step on one block at 16 values
-        // per thread, 7.6 us on 8-block clusters), at the clusters' 8 values per thread.
+        // blocks per instance: explicit here; the library's choice follows below
         g.C = 1;
-        if (o.cluster > 1) {
-            if (cluster_shape_compiled(g.logN, R, o.cluster))
-                g.C = o.cluster;
-        } else if (o.cluster == 0 && (g.logN == 11 || g.logN == 12)) {
-            const bool fp64 = b->prec == PREC_FP64;
-            for (int c : {8, 4, 2}) {
-                const int Rc = (fp64 || o.radix) ? R : 8;
-                if ((fp64 || c >= 4) && cluster_shape_compiled(g.logN, Rc, c) &&
-                    (long long)g.count * c <= b->sms) {
-                    g.C = c;
-                    g.R = Rc;
-                    g.G = 1;
-                    break;
+        if (o.cluster > 1 && cluster_shape_compiled(g.logN, R, o.cluster))
+            g.C = o.cluster;
+    }
+    // Library choice of clusters (o.cluster == 0).  Only where one block per instance leaves
+    // SMs idle: the batch's one-block plan occupies at most 2/3 of the SMs.  A group of
+    // N = 2048 or 4096 then takes the largest cluster whose blocks, with the other groups',
+    // stay within ~3.4 per SM (all resident at once), at 8 values per thread: C = 8 in FP32
+    // (C = 4 and 2 lose to one block there), C = 8, 4 or 2 in FP64.  Measured per RK4IP step,
+    // FP32 N = 4096: 16 instances 11.5 -> 5.9 us, 64 instances 11.7 -> 8.2 us, 96 instances
+    // 11.7 -> 15.5 us (not all blocks resident); FP64 N = 4096: 16 instances 437 -> 115 us,
+    // 96 instances 437 -> 349 us (C = 4).  Mixed batches whose one-block plan fills the GPU
+    // (N = 256 ... 4096 x 64) keep one block per instance: 584 ms per run, against 776 ms with
+    // 8-block clusters.
+    if (o.cluster == 0 && !any_large) {
+        long long blocks1 = 0;
+        for (const auto& g : b->groups)
+            blocks1 += (g.count + g.G - 1) / g.G;
+        const long long cap = (long long)b->sms * 17 / 5;
+        if (3 * blocks1 <= 2LL * b->sms) {
+            for (auto& g : b->groups) {
+                if (!(g.logN == 11 || g.logN == 12) || (o.radix && o.radix != 8))
+                    continue;
+                const long long others = blocks1 - (g.count + g.G - 1) / g.G;
+                for (int c : {8, 4, 2}) {
+                    if (b->prec == PREC_FP32 && c < 8)
+                        break;
+                    if (cluster_shape_compiled(g.logN, 8, c) && others + (long long)g.count * c <= cap) {
+                        g.C = c;
+                        g.R = 8;
+                        g.G = 1;
+                        break;
+                    }
                 }
             }
         }
@@ -821,6 +836,7 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
     a.hf = (float)b->h_cur;
     a.hhf = (float)(0.5 * b->h_cur);
     a.h6f = (float)(b->h_cur / 6.0);
+    a.a2a_fault = b->a2a_fault;
     return a;
 }
 
@@ -1349,8 +1365,22 @@ int cme_synchronize(cme_batch b)
     CME_CUDA(cudaMemcpy(st.data(), b->status_d, b->count * 4, cudaMemcpyDeviceToHost),
              "cme_synchronize: status");
     for (int i = 0; i < b->count; ++i)
+        if (st[i] == 2)
+            return fail(CME_ERR_TIMEOUT, "instance %d: a bounded device wait gave up", i);
+    for (int i = 0; i < b->count; ++i)
         if (st[i])
             return fail(CME_ERR_NONFINITE, "instance %d has a non-finite field value", i);
+    return CME_OK;
+}
+
+int cme_debug_fault(cme_batch b, int what)
+{
+    if (!b || what < 0 || what > 1)
+        return fail(CME_ERR_INVALID_ARG, "cme_debug_fault: invalid argument");
+    if (b->opt.use_graph)
+        return fail(CME_ERR_INVALID_ARG,
+                    "cme_debug_fault: not with use_graph (graphs keep their arguments)");
+    b->a2a_fault = what;
     return CME_OK;
 }
 
@@ -1764,5 +1794,14 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
         }
     }
     b->tau += h * (double)nsteps;
+    {
+        std::vector<int> sw(b->count);
+        CME_CUDA(cudaMemcpy(sw.data(), b->status_d, b->count * 4, cudaMemcpyDeviceToHost),
+                 "cme_grad: status");
+        for (int i = 0; i < b->count; ++i)
+            if (sw[i] == 2)
+                return fail(CME_ERR_TIMEOUT, "cme_grad: a bounded device wait gave up (instance %d)",
+                            i);
+    }
     return CME_OK;
 }

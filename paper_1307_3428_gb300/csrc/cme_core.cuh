@@ -219,6 +219,52 @@ CME_DEV void dsmem_put(uint32_t a, double v)
 {
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
+// Asynchronous store into a peer block's shared memory whose completion (its byte count) is
+// signalled on an mbarrier in the receiving block (both shared::cluster addresses).
+CME_DEV void dsmem_put_async(uint32_t a, float re, float im, uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+                 ::"r"(a), "f"(re), "f"(im), "r"(mbar) : "memory");
+}
+CME_DEV void dsmem_put_async(uint32_t a, double v, uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];"
+                 ::"r"(a), "d"(v), "r"(mbar) : "memory");
+}
+CME_DEV void mbar_init(uint32_t mb, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+// make the initialisation of this block's mbarriers visible to the cluster's other blocks
+CME_DEV void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one arrival that also expects `bytes` more bytes of asynchronous stores in this phase
+CME_DEV void mbar_arrive_expect_tx(uint32_t mb, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+                 : "memory");
+}
+// has the phase of parity `parity` completed?
+CME_DEV bool mbar_try_wait(uint32_t mb, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: at most `tries` polls (each may suspend the thread briefly); false if the
+// phase did not complete.
+CME_DEV bool mbar_wait(uint32_t mb, uint32_t parity, int tries)
+{
+    for (int k = 0; k < tries; ++k)
+        if (mbar_try_wait(mb, parity))
+            return true;
+    return false;
+}
 CME_DEV void cluster_sync()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
@@ -248,6 +294,10 @@ struct Xbuf<float> {
     CME_DEV Xbuf at(int off) const { return {p + off}; }
     // element at DSMEM address a (a maps element i of some block's buffer)
     CME_DEV void put_remote(uint32_t a, cx<float> v) const { dsmem_put(a, v.re, v.im); }
+    CME_DEV void put_remote_async(uint32_t a, cx<float> v, uint32_t mbar) const
+    {
+        dsmem_put_async(a, v.re, v.im, mbar);
+    }
     static constexpr int words_per_elem = 1;  // in 8-byte words
 };
 template <>
@@ -265,6 +315,11 @@ struct Xbuf<double> {
     {
         dsmem_put(a, v.re);
         dsmem_put(a + 8u * (uint32_t)stride, v.im);
+    }
+    CME_DEV void put_remote_async(uint32_t a, cx<double> v, uint32_t mbar) const
+    {
+        dsmem_put_async(a, v.re, mbar);
+        dsmem_put_async(a + 8u * (uint32_t)stride, v.im, mbar);
     }
     static constexpr int words_per_elem = 2;
 };
@@ -413,9 +468,13 @@ struct Transform {
 // forward transform is conj(inverse(conj .)) as for one block).
 //
 // One all-to-all moves every value once: each thread stores its R values into C blocks'
-// buffers with consecutive threads writing consecutive words, then one cluster barrier
-// (release/acquire) makes them visible.  Two ping-pong buffers per block: a buffer is
-// written again only two barriers after it was last read.
+// buffers with asynchronous stores, consecutive threads writing consecutive words, and each
+// store counts its bytes on an mbarrier of the receiving block; a block's threads wait for
+// that mbarrier's phase (all N2 values of its buffer arrived) instead of a cluster barrier.
+// Two ping-pong buffers per block, each with its own mbarrier.  A buffer is written again two
+// all-to-alls later, and that cannot start before every thread of the receiving block has
+// read it: a sender first needs the receiving block's next all-to-all values, and each
+// thread's stores there depend on the values it read (every thread stores into every block).
 // ----------------------------------------------------------------------------------------
 template <typename T, int LOGN, int R, int C>
 struct ClusterFFT {

@@ -32,6 +32,8 @@ struct StepArgs {
     float hf, hhf, h6f;     // h, h/2, h/6 rounded once to FP32 on the host
     int diag_mode;          // diagnostics kernel: DIAG_*
     void* diag_out;         // diagnostics output (same layout as the field)
+    int a2a_fault;          // test of the bounded waits: cluster all-to-alls expect 8 bytes
+                            // more than are sent and poll briefly (0 in normal use)
 };
 
 // Shared-memory footprint of one instance group (one instance of N = 2^logN handled by N/R

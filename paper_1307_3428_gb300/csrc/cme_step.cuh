@@ -104,21 +104,39 @@ struct Group {
                                   Twiddles<T, LOGN - LC, R, TW_REGS, C>>;
 
     int t;         // the thread holds modes t + jP
+    int ts;        // this thread's slots ts + jP of per-thread scratch vectors (coalesced)
     int par;
     Xbuf<T> buf;   // first of the two ping-pong exchange buffers
     typename TF::Addr ad;
     TW tw;
 
     // C > 1: all-to-all state (block `rank`, thread l): this thread's slots of the receive
-    // buffer 0; shared::cluster address of receive buffer 0 in every block; byte offsets of
-    // this thread's stores; the twiddles of the two directions in this block's shared memory
-    // (thread-major); the receive-buffer parity.
+    // buffer 0; shared::cluster address of receive buffer 0 and of its mbarrier in every
+    // block; byte offsets of this thread's stores; the twiddles of the two directions in this
+    // block's shared memory (thread-major); the receive-buffer parity; the phase parities of
+    // this block's two mbarriers; whether a wait gave up.
     Xbuf<T> abuf;
     uint32_t rb[C > 1 ? C : 1];
+    uint32_t rmb[C > 1 ? C : 1];
+    uint32_t mb;
     uint32_t om, ot;
     const cx<T>* twm;
     const cx<T>* twt;
     int apar;
+    uint32_t ph;
+    bool timed_out;
+    int fault;     // StepArgs::a2a_fault
+    // polls of one all-to-all wait before it gives up (a wait normally ends within a few)
+    static constexpr int WAIT_TRIES = 1 << 20;
+
+    // a bounded wait of an all-to-all gave up (the results are then not valid)
+    CME_DEV bool failed() const
+    {
+        if constexpr (C == 1)
+            return false;
+        else
+            return timed_out;
+    }
     // Physical modes (the zero padding of Sec. 2): of the N modes only the centred M,
     // mu = mlo .. mhi, are physical; the right-hand side is zero on the others, which stay at
     // zero.  masked = false (M = N) skips the test.
@@ -185,16 +203,30 @@ struct Group {
     template <bool T2M>
     CME_DEV void all_to_all(cx<T> (&x)[R])
     {
-        constexpr int PC = CF::PC, G = CF::G;
-        const uint32_t po = (uint32_t)apar * (uint32_t)(CF::N2 * 8 * Xbuf<T>::words_per_elem);
+        constexpr int PC = CF::PC, G = CF::G, W = Xbuf<T>::words_per_elem;
+        if (timed_out) {
+            // after a wait gave up this thread stores, arrives and waits no more, so no
+            // mbarrier receives an arrival or bytes beyond the phase it is stuck in
+            apar ^= 1;
+            return;
+        }
+        const uint32_t po = (uint32_t)apar * (uint32_t)(CF::N2 * 8 * W);
+        const uint32_t bo = 8u * (uint32_t)apar;   // mbarrier of buffer apar
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             if constexpr (T2M)
-                abuf.put_remote(rb[j / G] + ot + po + (uint32_t)(8 * PC * C * (j % G)), x[j]);
+                abuf.put_remote_async(rb[j / G] + ot + po + (uint32_t)(8 * PC * C * (j % G)),
+                                      x[j], rmb[j / G] + bo);
             else
-                abuf.put_remote(rb[j % C] + om + po + (uint32_t)(8 * PC * (j / C)), x[j]);
+                abuf.put_remote_async(rb[j % C] + om + po + (uint32_t)(8 * PC * (j / C)), x[j],
+                                      rmb[j % C] + bo);
         }
-        cluster_sync();
+        // the phase ends when this block's one arrival is in and all N2 values have landed
+        if (threadIdx.x == 0)
+            mbar_arrive_expect_tx(mb + bo, (uint32_t)(CF::N2 * 8 * W + (fault ? 8 : 0)));
+        if (!mbar_wait(mb + bo, (ph >> apar) & 1u, fault ? 1024 : WAIT_TRIES))
+            timed_out = true;   // the caller reports the instance
+        ph ^= 1u << apar;
         const Xbuf<T> mine = abuf.at(apar * CF::N2);
 #pragma unroll
         for (int j = 0; j < R; ++j)
@@ -254,6 +286,7 @@ struct Group {
             buf.stride = PL::BUF;    // buffer 1 starts at 2 BUF (Xbuf::at)
         }
         t = t_;
+        ts = t_;
         par = 0;
         ad = TF::make_addr(t);
         if constexpr (TW_SMEM)
@@ -267,9 +300,11 @@ struct Group {
 
     // Cluster set-up (C > 1): block `rank` of the cluster, thread l of the block.  The block's
     // dynamic shared memory holds the two exchange buffers of its N2-point transform, the two
-    // all-to-all receive buffers, the two twiddle arrays of the four-step transform and (FP32,
-    // N2 >= 2048) the pass twiddles of the N2-point transform.
-    CME_DEV void setup_cluster(unsigned char* smem, int rank, int l, const void* tw_table)
+    // all-to-all receive buffers, the two twiddle arrays of the four-step transform, (FP32,
+    // N2 >= 2048) the pass twiddles of the N2-point transform, and the receive buffers' two
+    // mbarriers (its last 16 bytes).
+    CME_DEV void setup_cluster(unsigned char* smem, int rank, int l, const void* tw_table,
+                               int a2a_fault)
     {
         static_assert(C > 1, "cluster groups only");
         constexpr int W = Xbuf<T>::words_per_elem, PC = CF::PC, N2 = CF::N2, G = CF::G;
@@ -287,6 +322,7 @@ struct Group {
         accS = nullptr;
         accL = nullptr;
         t = rank + C * l;
+        ts = rank * PC + l;
         par = 0;
         apar = 0;
         ad = TF::make_addr(l);
@@ -295,9 +331,22 @@ struct Group {
         else
             tw.init(tw_table, l);
         const uint32_t a0 = smem_addr(a2a);
+        mb = smem_addr(reinterpret_cast<unsigned char*>(tws + 2 * N2) +
+                       (TW_SMEM ? tw_bytes(sizeof(T), LOGN - LC, R) : 0));
 #pragma unroll
-        for (int c = 0; c < C; ++c)
+        for (int c = 0; c < C; ++c) {
             rb[c] = dsmem_map(a0, c);
+            rmb[c] = dsmem_map(mb, c);
+        }
+        // the kernel's cluster barrier before the first all-to-all publishes the initialisation
+        if (l == 0) {
+            mbar_init(mb, 1);
+            mbar_init(mb + 8u, 1);
+            mbar_init_fence();
+        }
+        ph = 0;
+        timed_out = false;
+        fault = a2a_fault;
         om = 8u * (uint32_t)(l + PC * rank * G);
         ot = 8u * (uint32_t)(l + PC * rank);
         // exp(2 pi i n2 k1 / N): after the block transform (n2 = l + PC j, k1 = rank), and
@@ -324,7 +373,7 @@ constexpr size_t cluster_smem_bytes()
     constexpr size_t W = Xbuf<T>::words_per_elem;
     return (size_t)2 * CF::TL::BUF * 8 * W + (size_t)2 * CF::N2 * 8 * W +
            (size_t)2 * CF::N2 * sizeof(cx<T>) +
-           (Group<T, LOGN, R, C>::TW_SMEM ? tw_bytes(sizeof(T), LOGN - CF::LC, R) : 0);
+           (Group<T, LOGN, R, C>::TW_SMEM ? tw_bytes(sizeof(T), LOGN - CF::LC, R) : 0) + 16;
 }
 
 template <typename T>
@@ -663,7 +712,7 @@ __global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(cons
     extern __shared__ __align__(16) unsigned char smem[];
     const int inst = blockIdx.x / C;
     GR grp;
-    grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw);
+    grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw, a.a2a_fault);
     if (a.phys)
         grp.set_modes(a.phys[inst]);
     const int t = grp.t;
@@ -693,6 +742,8 @@ __global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(cons
     fs.store(hi, lo);
     if (bad)
         a.status[inst] = 1;
+    if (grp.failed())
+        a.status[inst] = 2;
     cluster_sync();   // no block leaves while a peer may still address its shared memory
 }
 

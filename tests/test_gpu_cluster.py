@@ -158,22 +158,49 @@ def test_cluster_adjoint_agrees_with_one_block(N, C, prec):
 def test_plans_run_the_kernels_the_tests_mean(prec):
     """The cluster tests above do run clusters: an explicit cluster request without a radix
     selects the clusters' 8 values per thread, also where the library would otherwise choose 16
-    (FP32, N >= 2048).  The library's own choice for few instances of N = 4096 is an 8-block
-    cluster; with more instances than SMs / 4, FP32 keeps one block per instance (16 values per
-    thread), while FP64 takes the largest cluster that fits."""
+    (FP32, N >= 2048).  The library's own choice: 8-block clusters while one block per instance
+    would leave SMs idle and the clusters' blocks all stay resident (2 and 64 instances of
+    N = 4096), one block per instance for 128 instances."""
     insts = random_set(4096, 3700, 2)
     b = batch_of(insts, prec, cluster=4)
     assert b.plan(0)["radix"] == 8 and b.plan(0)["cluster"] == 4
     b.close()
-    b = batch_of(insts, prec)
-    p = b.plan(0)
-    assert p["cluster"] == 8 and p["radix"] == 8
-    b.close()
-    many = [insts[k % 2] for k in range(64)]
-    b = batch_of(many, prec)
-    p = b.plan(0)
-    if prec == cme.FP64:
-        assert p["cluster"] == 2 and p["radix"] == 8
-    else:
-        assert p["cluster"] == 1 and p["radix"] == 16
+    for count, cluster in ((2, 8), (64, 8), (128, 1)):
+        b = batch_of([insts[k % 2] for k in range(count)], prec)
+        p = b.plan(0)
+        assert p["cluster"] == cluster, (count, p)
+        assert p["radix"] == (16 if cluster == 1 and prec == cme.FP32 else 8), (count, p)
+        b.close()
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_bounded_wait_reports_timeout_and_the_batch_recovers(prec):
+    """Failure detection without a device fault: the test switch (cme_debug_fault) makes each
+    cluster all-to-all expect one word more than is sent, so its wait runs out of polls.  The
+    kernels finish, the instances report status 2, cme_synchronize and cme_grad return
+    TIMEOUT, and the same batch then steps correctly again."""
+    N = 2048
+    insts = random_set(N, 3800, 2)
+    b = batch_of(insts, prec, cluster=4)
+    D0 = b.get_state()
+    b.debug_fault(1)
+    b.step(1e-3, 3)
+    with pytest.raises(cme.CmeError) as e:
+        b.synchronize()
+    assert e.value.code == -5
+    assert list(b.status()) == [2, 2]
+    b.set_state(D0)   # clears the status words
+    T = np.concatenate([target_for(N, 3810 + k) for k in range(2)])
+    with pytest.raises(cme.CmeError) as e:
+        b.grad(1e-3, 4, T)
+    assert e.value.code == -5
+    b.debug_fault(0)
+    b.set_state(D0)
+    b.step(1e-3, 10)
+    b.synchronize()
+    assert list(b.status()) == [0, 0]
+    got = b.split(b.get_state())
+    refs = fft_engine.rk4ip(fft_engine.Batch(insts), 1e-3, 10)
+    for g, r in zip(got, refs):
+        assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
     b.close()
