@@ -319,6 +319,8 @@ def run_gpu(args, world, rank, local):
         w = wl.octave()
     elif args.workload == "fig1":
         w = wl.fig1()
+    elif args.workload == "forward4096":
+        w = wl.adjoint4096()   # the gradient workload's instances, forward steps only
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     strang = args.strang or args.workload == "fig1"   # Fig. 1 is a split-step run
@@ -514,6 +516,8 @@ def run_gpu(args, world, rank, local):
         line["retimed_after_low_fma_rate"] = True
     if plan is not None:
         line["config"]["plan"] = plan
+    elif len(set(sizes)) == 1:
+        line["config"]["launch_plan"] = b32.plan(0)
     if args.workload == "fig1":
         # the whole ensemble (4 runs of tau~ = 128 pi) in FP64 as well; the paper quotes 54 s
         # for it on a desktop computer (context, not a target)
@@ -571,7 +575,8 @@ def main():
     ap.add_argument("--radix", type=int, default=0, help="field values per thread (0: default)")
     ap.add_argument("--inst-per-cta", type=int, default=0, help="instances per block (0: default)")
     ap.add_argument("--workload", default="sweep512",
-                    choices=["sweep512", "uneven", "plain64", "octave", "adjoint", "fig1"],
+                    choices=["sweep512", "uneven", "plain64", "octave", "adjoint", "fig1",
+                             "forward4096"],
                     help="sweep512 is the headline workload; the others are secondary records")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2, 4, 8],

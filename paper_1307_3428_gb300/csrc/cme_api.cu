@@ -155,6 +155,7 @@ struct LaunchGroup {
     // N > 4096: four-step split N = N1 N2 (column length N1, row length N2)
     bool large = false;
     int logN1 = 0, logN2 = 0, G1 = 1, G2 = 1;
+    int RL = 8;                 // values per thread of the row and column kernels
     void* Y = nullptr;          // [count][N] inter-pass buffers
     void* Z = nullptr;
     cudaGraphExec_t chunk = nullptr;   // LARGE_CHUNK steps, replayed by cme_step
@@ -279,9 +280,11 @@ int plan_batch(cme_batch b, const cme_options& o)
     bool any_large = false;
     for (auto& g : b->groups) {
         if (g.large) {
-            // rows of N2 and columns of N1 values, 8 per thread; whole warps per block
-            auto blocks_of = [](int len) {
-                const int P = len / 8;
+            // rows of N2 and columns of N1 values, RL per thread (8, or 4 on request where
+            // compiled: N1, N2 in 2^8 ... 2^10); whole warps per block
+            g.RL = (o.radix == 4 && g.logN2 >= 8 && g.logN1 <= 10) ? 4 : 8;
+            auto blocks_of = [&g](int len) {
+                const int P = len / g.RL;
                 return P >= 64 ? 1 : std::max(1, 64 / P);
             };
             g.G1 = blocks_of(1 << g.logN1);
@@ -896,8 +899,8 @@ cudaError_t large_row(cme_batch b, const LaunchGroup& g, LargeArgs a, cudaStream
     a.G = g.G2;
     ++g_launches;
     const long long rows = (long long)g.count << g.logN1;
-    return b->prec == PREC_FP64 ? launch_large_row_fp64(g.logN2, a, rows, st, pdl)
-                                : launch_large_row_fp32(g.logN2, a, rows, st, pdl);
+    return b->prec == PREC_FP64 ? launch_large_row_fp64(g.logN2, g.RL, a, rows, st, pdl)
+                                : launch_large_row_fp32(g.logN2, g.RL, a, rows, st, pdl);
 }
 
 cudaError_t large_col(cme_batch b, const LaunchGroup& g, LargeArgs a, int stage, cudaStream_t st,
@@ -907,8 +910,8 @@ cudaError_t large_col(cme_batch b, const LaunchGroup& g, LargeArgs a, int stage,
     a.stage = stage;
     ++g_launches;
     const long long cols = (long long)g.count << g.logN2;
-    return b->prec == PREC_FP64 ? launch_large_col_fp64(g.logN1, a, cols, st, pdl)
-                                : launch_large_col_fp32(g.logN1, a, cols, st, pdl);
+    return b->prec == PREC_FP64 ? launch_large_col_fp64(g.logN1, g.RL, a, cols, st, pdl)
+                                : launch_large_col_fp32(g.logN1, g.RL, a, cols, st, pdl);
 }
 
 // One RK4IP step of a four-step group: [row, col] for each of the four stages; the last column

@@ -197,12 +197,16 @@ cudaError_t launch_fused_fp64(int method, const FusedArgs& a, int grid, size_t s
 namespace cme {
 struct LargeArgs;
 // pdl = true launches with programmatic stream serialisation (cme_large.cuh: pdl_wait)  // cme_large.cuh
-cudaError_t launch_large_row_fp32(int logN2, const LargeArgs& a, long long rows, cudaStream_t s,
+cudaError_t launch_large_row_fp32(int logN2, int R, const LargeArgs& a, long long rows,
+                                  cudaStream_t s,
                                   bool pdl);
-cudaError_t launch_large_row_fp64(int logN2, const LargeArgs& a, long long rows, cudaStream_t s,
+cudaError_t launch_large_row_fp64(int logN2, int R, const LargeArgs& a, long long rows,
+                                  cudaStream_t s,
                                   bool pdl);
-cudaError_t launch_large_col_fp32(int logN1, const LargeArgs& a, long long cols, cudaStream_t s,
+cudaError_t launch_large_col_fp32(int logN1, int R, const LargeArgs& a, long long cols,
+                                  cudaStream_t s,
                                   bool pdl);
-cudaError_t launch_large_col_fp64(int logN1, const LargeArgs& a, long long cols, cudaStream_t s,
+cudaError_t launch_large_col_fp64(int logN1, int R, const LargeArgs& a, long long cols,
+                                  cudaStream_t s,
                                   bool pdl);
 }  // namespace cme

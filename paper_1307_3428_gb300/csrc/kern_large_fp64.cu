@@ -4,14 +4,16 @@
 
 namespace cme {
 
-#define CME_LARGE_SHAPES(X) X(6, 8) X(7, 8) X(8, 8) X(9, 8) X(10, 8)
+#define CME_LARGE_SHAPES(X) \
+    X(6, 8) X(7, 8) X(8, 8) X(9, 8) X(10, 8) X(8, 4) X(9, 4) X(10, 4)
 
-cudaError_t launch_large_row_fp64(int logN2, const LargeArgs& a, long long rows, cudaStream_t s,
+cudaError_t launch_large_row_fp64(int logN2, int R, const LargeArgs& a, long long rows,
+                                  cudaStream_t s,
                                   bool pdl)
 {
-    switch (logN2) {
+    switch (logN2 * 32 + R) {
 #define CME_CASE(LN, RR)                                                          \
-    case LN: {                                                                    \
+    case LN * 32 + RR: {                                                                    \
         constexpr int P = Plan<LN, RR>::P;                                        \
         const size_t smem = smem_bytes_for<double>(LN, RR, a.G);                    \
         auto k = large_row_kernel<double, LN, RR>;                                  \
@@ -24,12 +26,13 @@ cudaError_t launch_large_row_fp64(int logN2, const LargeArgs& a, long long rows,
     }
 }
 
-cudaError_t launch_large_col_fp64(int logN1, const LargeArgs& a, long long cols, cudaStream_t s,
+cudaError_t launch_large_col_fp64(int logN1, int R, const LargeArgs& a, long long cols,
+                                  cudaStream_t s,
                                   bool pdl)
 {
-    switch (logN1) {
+    switch (logN1 * 32 + R) {
 #define CME_CASE(LN, RR)                                                          \
-    case LN: {                                                                    \
+    case LN * 32 + RR: {                                                                    \
         constexpr int P = Plan<LN, RR>::P;                                        \
         const size_t smem = smem_bytes_for<double>(LN, RR, a.G);                    \
         auto k = large_col_kernel<double, LN, RR>;                                  \

@@ -117,3 +117,23 @@ def test_largest_sizes(prec):
     got = b.get_state()
     ref = fft_engine.rk4ip(fft_engine.Batch(insts), 1e-4, 10)[0]
     assert rel(got, ref) <= (1e-12 if prec == cme.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+@pytest.mark.parametrize("N", [65536, 131072])
+def test_four_values_per_thread(N, prec):
+    """radix = 4 runs the row and column kernels at 4 values per thread (N1, N2 >= 256):
+    transform against numpy.fft, and RK4IP against the Eq. 4 engine."""
+    insts = [wl.random_instance(N, 2500 + k, amp=0.3 * np.sqrt(64.0 / N), D2=1e-4)
+             for k in range(2)]
+    b = batch_of(insts, prec, radix=4)
+    got = b.split(b.transform(+1))
+    for g, inst in zip(got, insts):
+        ref = np.fft.ifft(np.fft.ifftshift(inst.D0)) * N
+        tol = 1e-13 if prec == cme.FP64 else 2e-6
+        assert np.max(np.abs(g - ref)) <= tol * np.max(np.abs(ref)) * np.log2(N)
+    b.step(1e-4, 40)
+    got = b.split(b.get_state())
+    refs = fft_engine.rk4ip(fft_engine.Batch(insts), 1e-4, 40)
+    for g, r in zip(got, refs):
+        assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
