@@ -175,6 +175,51 @@ def oracle_sample(target_s: float, sweep_index: int = 128, fixed_steps: int | No
     return inst.N * steps / dt, steps, dt, D
 
 
+def _oracle_instance_run(job):
+    """One process of the all-cores oracle timing: `steps` RK4IP steps of sweep instance
+    `index` with the direct-sum oracle as it stands."""
+    index, steps = job
+    import oracle
+    from paper_1307_3428_gb300 import workloads as wl
+    inst = wl.sweep512(indices=[index]).instances[0]
+    oracle.integrate(inst, 5e-4, steps, oracle.RK4IP)
+    return inst.N * steps
+
+
+def oracle_all_cores(rate1: float, target_s: float):
+    """The direct-sum oracle on every host core: one sweep instance per process (a spawn
+    pool), each for about target_s seconds at the single-core rate rate1.  Returns
+    (mode-steps/s, processes, steps per instance, seconds)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    n = os.cpu_count() or 1
+    steps = max(1, int(target_s * rate1 / 512))
+    # a worker that dies raises BrokenProcessPool here instead of being replaced forever
+    with ProcessPoolExecutor(n, mp_context=mp.get_context("spawn")) as pool:
+        list(pool.map(_oracle_instance_run, [(k, 1) for k in range(n)]))   # start-up
+        t0 = time.perf_counter()
+        work = sum(pool.map(_oracle_instance_run, [(k, steps) for k in range(n)]))
+        dt = time.perf_counter() - t0
+    return work / dt, n, steps, dt
+
+
+def fft_engine_sample(target_s: float):
+    """The oracle's numpy Eq. 4 engine (the paper's method on the CPU) on the whole
+    256-instance sweep, vectorised over the batch, for about target_s seconds."""
+    from oracle import fft_engine
+    from paper_1307_3428_gb300 import workloads as wl
+    w = wl.sweep512()
+    fb = fft_engine.Batch(w.instances)
+    t0 = time.perf_counter()
+    fft_engine.rk4ip(fb, w.h, 2)
+    per_step = (time.perf_counter() - t0) / 2
+    steps = max(1, int(target_s / max(per_step, 1e-6)))
+    t0 = time.perf_counter()
+    fft_engine.rk4ip(fb, w.h, steps)
+    dt = time.perf_counter() - t0
+    return sum(i.N for i in w.instances) * steps / dt, steps, dt
+
+
 def run_reference(args, world, rank):
     """CPU oracle arm: rank 0 times the oracle as it stands on bounded samples."""
     if rank != 0:
@@ -558,6 +603,23 @@ def run_gpu(args, world, rank, local):
                                 "sample": f"1 instance (N=512, sigma index 128) x {steps} RK4IP "
                                           f"steps, FP64 direct O(N^3) sum, {dt:.1f} s"}
         line["error"]["gpu_vs_oracle_sample"] = {"fp32": e32, "fp64": e64, "steps": steps}
+        # context beside the single-core baseline: the direct oracle on every host core, and
+        # the oracle's numpy Eq. 4 engine (numpy's FFT runs on one thread)
+        try:
+            r_all, procs, st_all, dt_all = oracle_all_cores(rate, args.ref_seconds)
+            all_cores = {
+                "value": r_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+                "sample": f"{procs} sweep instances, one per process, x {st_all} RK4IP steps, "
+                          f"FP64 direct O(N^3) sum, {dt_all:.1f} s"}
+        except Exception as e:   # context only: the line stands without it
+            all_cores = {"unavailable": f"{type(e).__name__}: {e}"}
+        r_fft, st_fft, dt_fft = fft_engine_sample(args.ref_seconds / 2)
+        line["cpu_context"] = {
+            "direct_oracle_all_cores": all_cores,
+            "eq4_engine_one_core": {
+                "value": r_fft, "unit": UNIT, "cores": 1, "kind": "oracle (numpy Eq. 4 engine)",
+                "sample": f"256 x 512 sweep x {st_fft} RK4IP steps, FP64 numpy.fft, "
+                          f"{dt_fft:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
