@@ -95,6 +95,35 @@ CME_DEV int adj_setup(Group<T, LOGN, R, C>& grp, unsigned char* smem, const Step
 template <int LOGN, int R, int C>
 constexpr int adj_threads() { return C == 1 ? max_threads<LOGN, R>() : Plan<LOGN, R>::P / C; }
 
+// FP32 backward kernels of cluster groups prefetch the stored data of the next step (ADJ_VECS
+// vectors, R chunks of P/C values each per block) into shared memory with bulk asynchronous
+// copies while they process the current one, where two steps' worth fits beside the cluster
+// transform's buffers (N = 4096 x 16 gradient: 219 -> 188 ms).  FP64 gradients run their
+// recomputation and backward blocks on shared SMs (8-block clusters), which the larger
+// block would no longer allow (2.4e8 -> 1.4e8 gradient mode-steps/s), and FP64 steps are
+// bound by the FP64 pipes, not by these loads.
+template <typename T, int LOGN, int R, int C>
+CME_HD constexpr size_t adj_prefetch_bytes()
+{
+    return C > 1 ? (size_t)2 * ADJ_VECS * R * (Plan<LOGN, R>::P / C) * sizeof(cx<T>) : 0;
+}
+template <typename T, int LOGN, int R, int C>
+CME_HD constexpr bool adj_prefetch()
+{
+    if constexpr (C == 1 || sizeof(T) != 4)
+        return false;
+    else
+        return cluster_smem_bytes<T, LOGN, R, C>() + adj_prefetch_bytes<T, LOGN, R, C>() + 16 <=
+               (size_t)200 * 1024;
+}
+// dynamic shared memory of the backward kernel of a cluster group
+template <typename T, int LOGN, int R, int C>
+CME_HD constexpr size_t adj_backward_smem()
+{
+    return cluster_smem_bytes<T, LOGN, R, C>() +
+           (adj_prefetch<T, LOGN, R, C>() ? adj_prefetch_bytes<T, LOGN, R, C>() + 16 : 0);
+}
+
 // Recompute role: the states of segment A.seg from its checkpoint, the stage values y1, k2, k3
 // and the time-domain fields of the four stage inputs of every step, into half (A.seg mod 2)
 // of A.stages.
@@ -179,14 +208,64 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
         pb = A.pbar[inst];
     const T hh = c.hh, h = c.h, h6 = c.h6, h3 = T(2) * c.h6;
     const T gNn = c.gN;  // g0 / N
+
+    // Prefetch (cluster groups): chunk q = v R + j of step i is the block's PC consecutive
+    // slots of vector v, element j, at pf[(buffer i mod 2) CH + q][PC]; thread l reads slot l.
+    constexpr bool PF = adj_prefetch<T, LOGN, R, C>();
+    constexpr int PC = P / C, CH = ADJ_VECS * R;
+    cx<T>* pf = nullptr;
+    uint32_t pmb = 0, pph = 0;
+    bool pf_failed = false;
+    const int l = (int)threadIdx.x;
+    if constexpr (PF) {
+        pf = reinterpret_cast<cx<T>*>(smem + cluster_smem_bytes<T, LOGN, R, C>());
+        pmb = smem_addr(smem + cluster_smem_bytes<T, LOGN, R, C>() +
+                        adj_prefetch_bytes<T, LOGN, R, C>());
+        if (l == 0) {
+            mbar_init(pmb, 1);
+            mbar_init(pmb + 8u, 1);
+        }
+    }
+    // copies of step i into buffer i mod 2 (buf - l: the block's first slot)
+    auto issue = [&](long long i) {
+        const int b = (int)(i & 1);
+        if (l == 0)
+            mbar_arrive_expect_tx(pmb + 8u * b, (uint32_t)(CH * PC * sizeof(cx<T>)));
+        for (int q = l; q < CH; q += PC)
+            bulk_g2s(smem_addr(pf + (size_t)(b * CH + q) * PC),
+                     buf - l + i * ADJ_VECS * TT + (q / R) * TT + (q % R) * P,
+                     (uint32_t)(PC * sizeof(cx<T>)), pmb + 8u * b);
+    };
     if constexpr (C > 1)
         cluster_sync();   // every block of the cluster runs before the first remote store
+                          // (and this block's threads see its mbarriers initialised)
+    if constexpr (PF)
+        issue(ns - 1);
 
     for (long long i = ns - 1; i >= 0; --i) {
         // step i: D, then y1, k2, k3, then a of the stage inputs D, x2, x3, x4, at TT strides
         const cx<T>* Dn = buf + i * ADJ_VECS * TT;
-        const cx<T>* yb = Dn + TT;
-        const cx<T>* ab = Dn + 4 * TT;
+        const cx<T>* sb = nullptr;
+        if constexpr (PF) {
+            // buffer (i - 1) mod 2 held step i + 1, which every thread has finished with
+            __syncthreads();
+            if (i >= 1 && !pf_failed) {
+                fence_proxy_async_smem();
+                issue(i - 1);
+            }
+            const int b = (int)(i & 1);
+            if (!pf_failed && !mbar_wait(pmb + 8u * b, (pph >> b) & 1u, 1 << 20))
+                pf_failed = true;   // reported below; the results are then not valid
+            pph ^= 1u << b;
+            sb = pf + (size_t)b * CH * PC + l;
+        }
+        // vector v (0: D, 1..3: y1, k2, k3, 4 + st: a of stage input st), element j
+        auto ld = [&](int v, int j) -> cx<T> {
+            if constexpr (PF)
+                return sb[(v * R + j) * PC];
+            else
+                return Dn[(long long)v * TT + j * P];
+        };
         // reverse stages 3 (x4), 2 (x3), 1 (x2), 0 (D)
         cx<T> ub[R], cot[R];
 #pragma unroll 1
@@ -198,8 +277,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     const cx<T> E = pr.getE(j);
-                    const cx<T> u = cmul(E, Dn[j * P]);
-                    const cx<T> y1 = yb[j * P], k2 = yb[TT + j * P], k3 = yb[2 * TT + j * P];
+                    const cx<T> u = cmul(E, ld(0, j));
+                    const cx<T> y1 = ld(1, j), k2 = ld(2, j), k3 = ld(3, j);
                     cot[j] = cscale(Db[j], h6);
                     const cx<T> w = caxpy(u, h6, cadd(cmul(E, y1), cscale(cadd(k2, k3), T(2))));
                     gl[j].add(cmulc(cmulc(Db[j], w), cscale(E, hh)));
@@ -212,7 +291,6 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
             // zbar = J_F(z)^H cot, a = IDFT(stage input) from the buffer: bbar =
             // IDFT(-i (g0/N) cot), then DFT(2 |a|^2 bbar + a^2 conj(bbar)) (two transforms
             // through one call site)
-            const cx<T>* as = ab + st * TT;
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 z[j] = {gNn * cot[j].im, -gNn * cot[j].re};
@@ -222,7 +300,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                 if (p == 1) {
 #pragma unroll
                     for (int j = 0; j < R; ++j) {
-                        const cx<T> a = as[j * P];
+                        const cx<T> a = ld(4 + st, j);
                         const cx<T> bb = z[j];                   // bbar
                         const T p2 = a.re * a.re + a.im * a.im;
                         const cx<T> a2 = cmul(a, a);
@@ -245,8 +323,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                 const cx<T> wb = cmulc(Db[j], E);                // conj(E) Dbar'
                 const cx<T> hE = cscale(E, hh);
                 if (st == 3) {
-                    const cx<T> u = cmul(E, Dn[j * P]);
-                    const cx<T> v = caxpy(u, h, yb[2 * TT + j * P]);
+                    const cx<T> u = cmul(E, ld(0, j));
+                    const cx<T> v = caxpy(u, h, ld(3, j));
                     const cx<T> vb = cmulc(xb, E);               // conj(E) x4bar
                     gl[j].add(cmulc(cmulc(xb, v), hE));          // conj(hh E) conj(v) x4bar
                     ub[j] = cadd(wb, vb);
@@ -257,8 +335,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                 } else {   // st == 1
                     ub[j] = cadd(ub[j], xb);
                     const cx<T> k1b = caxpy(cscale(wb, h6), hh, xb);
-                    const cx<T> y1 = yb[j * P];
-                    const cx<T> D = Dn[j * P];
+                    const cx<T> y1 = ld(1, j);
+                    const cx<T> D = ld(0, j);
                     gl[j].add(cmulc(cmulc(ub[j], D), hE));       // conj(hh E) conj(D) ubar
                     gl[j].add(cmulc(cmulc(k1b, y1), hE));        // conj(hh E) conj(y1) k1bar
                     Db[j] = cmulc(ub[j], E);                     // conj(E) ubar
@@ -276,7 +354,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
         if (t == 0)
             A.pbar[inst] = pb;
     }
-    if (grp.failed() && a.status)
+    if ((grp.failed() || pf_failed) && a.status)
         a.status[inst] = 2;
     if constexpr (C > 1)
         cluster_sync();   // no block leaves while a peer may still address its shared memory

@@ -265,6 +265,20 @@ CME_DEV bool mbar_wait(uint32_t mb, uint32_t parity, int tries)
             return true;
     return false;
 }
+// Bulk asynchronous copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global memory into this block's shared memory, its completion counted on mbarrier `mbar`.
+CME_DEV void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes),
+                 "r"(mbar) : "memory");
+}
+// order this thread's earlier generic-proxy accesses of shared memory before its later
+// asynchronous-proxy writes (bulk copies) into it
+CME_DEV void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 CME_DEV void cluster_sync()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"

@@ -367,7 +367,7 @@ struct Group {
 
 // Dynamic shared memory of one block of a cluster group: two exchange buffers.
 template <typename T, int LOGN, int R, int C>
-constexpr size_t cluster_smem_bytes()
+CME_HD constexpr size_t cluster_smem_bytes()
 {
     using CF = ClusterFFT<T, LOGN, R, C>;
     constexpr size_t W = Xbuf<T>::words_per_elem;

@@ -16,7 +16,7 @@ cudaError_t launch_adjoint_cluster_fp64(int role, int logN, int R, int C, const 
                                       cluster_smem_bytes<double, LN, RR, CC>(), CC, s, a)     \
                    : launch_clustered(adjoint_kernel<double, LN, RR, CC>, a.s.ninst * CC,     \
                                       Plan<LN, RR>::P / CC,                                \
-                                      cluster_smem_bytes<double, LN, RR, CC>(), CC, s, a);
+                                      adj_backward_smem<double, LN, RR, CC>(), CC, s, a);
         CME_FOR_EACH_CLUSTER_SHAPE(CME_CASE)
 #undef CME_CASE
     default:
