@@ -318,7 +318,7 @@ int plan_batch(cme_batch b, const cme_options& o)
     // 96 instances 437 -> 349 us (C = 4).  Mixed batches whose one-block plan fills the GPU
     // (N = 256 ... 4096 x 64) keep one block per instance: 584 ms per run, against 776 ms with
     // 8-block clusters.
-    if (o.cluster == 0 && !any_large) {
+    if (o.cluster == 0 && !any_large && o.persistent != 2) {   // the work-list kernel has no clusters
         long long blocks1 = 0;
         for (const auto& g : b->groups)
             blocks1 += (g.count + g.G - 1) / g.G;

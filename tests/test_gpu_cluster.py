@@ -204,3 +204,27 @@ def test_bounded_wait_reports_timeout_and_the_batch_recovers(prec):
     for g, r in zip(got, refs):
         assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
     b.close()
+
+
+@pytest.mark.parametrize("segment", [1, 2, 7])
+def test_cluster_adjoint_segment_lengths(segment):
+    """The FP32 backward kernel on clusters prefetches the next step's stored data into shared
+    memory (two buffers, bulk copies).  Segments of 1, 2 and 7 steps cover the single-step
+    segment and both buffer parities; each gradient must be as close to the one-block FP64
+    gradient as the one-block FP32 gradient is (within 4 times its error, or 1e-5)."""
+    N = 4096
+    insts = [wl.make_instance(N, 0.01, 1e-4, 2.0 + k, 2.0, 1e-3, seed=3900 + k) for k in range(2)]
+    T = np.concatenate([target_for(N, 3910 + k) for k in range(2)])
+
+    def grad(p, c, seg):
+        b = batch_of(insts, p, radix=8, cluster=c)
+        g = b.grad(2e-4, 15, T, segment=seg)
+        b.close()
+        return g
+
+    ref = grad(cme.FP64, 1, 5)
+    one = grad(cme.FP32, 1, 5)
+    got = grad(cme.FP32, 4, segment)
+    for key in ref:
+        e1, eC = rel(one[key], ref[key]), rel(got[key], ref[key])
+        assert eC <= max(4 * e1, 1e-5), (key, e1, eC)
