@@ -65,7 +65,9 @@ typedef struct cme_batch_s* cme_batch;
 typedef struct cme_options {
     int precision;         /* CME_FP64 or CME_FP32 */
     int integrator;        /* CME_RK4IP or CME_STRANG */
-    int radix;             /* field elements per thread (4, 8 or 16); 0 = library choice */
+    int radix;             /* field elements per thread (4, 8 or 16); 0 = library choice.
+                              For N > 4096, 4 selects the row and column kernels at 4 values
+                              per thread where compiled (N1, N2 in 2^8 ... 2^10), else 8 */
     int inst_per_cta;      /* instances sharing one thread block; 0 = library choice */
     long steps_per_launch; /* steps per kernel launch; 0 = all steps of a call in one launch */
     int use_graph;         /* 1 = cme_step replays a cached CUDA graph per (h, nsteps) */
@@ -79,12 +81,16 @@ typedef struct cme_options {
                               distributed shared memory, C-point transforms in registers;
                               one kernel per N group; also used by cme_grad).  With radix 0,
                               a cluster request selects the clusters' 8 values per thread.
-                              0 = library choice: the largest C with instances * C <= SMs,
-                              where C >= 4 in FP32 (FP32 steps are latency bound and a
-                              2-block cluster does not repay its all-to-all); FP32 gradients
-                              take the largest C with 2 * instances * C <= SMs, since their
-                              recomputation and backward kernels run side by side.  Groups
-                              without a compiled cluster shape run C = 1. */
+                              0 = library choice: clusters only where one block per
+                              instance would leave SMs idle (the batch's one-block plan uses
+                              at most 2/3 of them) and not with persistent = 2; a group of
+                              N = 2048 or 4096 then takes the largest C whose blocks, with
+                              the other groups', stay within ~3.4 per SM: C = 8 in FP32
+                              (smaller FP32 clusters do not repay their all-to-all), C = 8,
+                              4 or 2 in FP64.  FP32 gradients take the largest C in {8, 4}
+                              with 2 * instances * C <= SMs, since their recomputation and
+                              backward kernels run side by side.  Groups without a compiled
+                              cluster shape run C = 1. */
 } cme_options;
 
 /* Fill *opt with the defaults: CME_FP64, CME_RK4IP, library-chosen launch shape, no graph. */
