@@ -105,7 +105,7 @@ def make_instance(N: int, D2: float, D3: float, sigma: float, A_in: complex, noi
 
 
 # --------------------------------------------------------------------------------------
-# The five synthetic workloads.  Readings for parameters the workload list leaves open:
+# The synthetic workloads.  Readings for parameters the workload list leaves open:
 # kappa_mu = 1, kappa_ext = 0.5, g0 = 1 wherever not stated.
 # --------------------------------------------------------------------------------------
 
