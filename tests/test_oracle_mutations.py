@@ -4,7 +4,9 @@ index or sign, a dropped or wrong Runge-Kutta term, the pump on the wrong mode, 
 normalisation, a wrong mode band, a wrong step in the adjoint), compiles it with the oracle's
 own flags, and runs the committed pin suites (test_oracle_pins, test_oracle_adjoint,
 test_oracle_padding) in a child process whose oracle calls all go to the modified build.  The
-unmodified source must pass them; every mutant must fail at least one.  CPU only."""
+same is done for the oracle's numpy Eq. 4 engine (`oracle/fft_engine.py`) through a copy of the
+package.  The unmodified sources must pass the pins; every mutant must fail at least one.
+CPU only."""
 import os
 import subprocess
 import sys
@@ -107,4 +109,56 @@ def test_planted_mistake_is_caught(tmp_path, name):
     text = open(SRC).read()
     assert text.count(old) == 1, name
     rc, out = run_pins(compile_oracle(text.replace(old, new), tmp_path))
+    assert rc == 1, f"{name}: pins exit {rc}\n{out}"
+
+
+# The oracle's numpy Eq. 4 engine (fft_engine.py), pinned to the direct engine: the same
+# planted-mistake check through a copy of the oracle package with one edit in fft_engine.py.
+ENGINE_MUTATIONS = {
+    "Eq. 4: missing 1/N": ("return _to_centred(np.fft.fft(np.abs(a) ** 2 * a, axis=-1) / N)",
+                           "return _to_centred(np.fft.fft(np.abs(a) ** 2 * a, axis=-1))"),
+    "Eq. 4: padding modes keep their FWM term": ("        out = np.where(self.mask, out, 0.0)\n",
+                                                 ""),
+    "engine: detuning sign": ("1j * (self.omega - om0 - self.sigma)",
+                              "1j * (self.omega - om0 + self.sigma)"),
+    "engine RK4IP: missing propagator on the last stage": (
+        "k4 = batch.F(E * (AI + h * k3), linear)", "k4 = batch.F(AI + h * k3, linear)"),
+    "engine Strang: half the Kerr phase": (
+        "a = a * np.exp(1j * batch.g0 * np.abs(a) ** 2 * h)",
+        "a = a * np.exp(1j * batch.g0 * np.abs(a) ** 2 * 0.5 * h)"),
+    "engine Strang: pump increment": ("(e[:, N // 2] - 1.0) / np.where", "e[:, N // 2] / np.where"),
+}
+
+
+def run_pins_with_oracle_copy(tmp_path, edit=None):
+    """Exit code of the pin suites with `import oracle` resolving to a copy of the package in
+    tmp_path (its C library built there), fft_engine.py edited by `edit` = (old, new)."""
+    import shutil
+    dst = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), dst,
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    if edit:
+        p = dst / "fft_engine.py"
+        text = p.read_text()
+        assert text.count(edit[0]) == 1, edit[0]
+        p.write_text(text.replace(edit[0], edit[1]))
+    code = ("import sys, pytest, oracle; "
+            "assert oracle.__file__.startswith(sys.argv[1]), oracle.__file__; "
+            "sys.exit(pytest.main(['-x', '-q', '-p', 'no:cacheprovider', '-m', 'not gpu', "
+            "'--rootdir', sys.argv[2]] + sys.argv[3:]))")
+    env = dict(os.environ, PYTHONPATH=str(tmp_path) + os.pathsep + ROOT)
+    suites = [os.path.join(ROOT, s) for s in PIN_SUITES]
+    r = subprocess.run([sys.executable, "-c", code, str(tmp_path), ROOT, *suites],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:] + r.stderr[-1000:]
+
+
+def test_unmodified_engine_copy_passes_the_pins(tmp_path):
+    rc, out = run_pins_with_oracle_copy(tmp_path)
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", list(ENGINE_MUTATIONS))
+def test_planted_mistake_in_the_eq4_engine_is_caught(tmp_path, name):
+    rc, out = run_pins_with_oracle_copy(tmp_path, ENGINE_MUTATIONS[name])
     assert rc == 1, f"{name}: pins exit {rc}\n{out}"
