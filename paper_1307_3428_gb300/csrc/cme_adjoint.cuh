@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
         if (l == 0) {
             mbar_init(pmb, 1);
             mbar_init(pmb + 8u, 1);
+            mbar_init_fence();   // visible to the bulk copies that complete on them
         }
     }
     // copies of step i into buffer i mod 2 (buf - l: the block's first slot)
