@@ -155,6 +155,18 @@ def max_over_ranks(x: float, world: int) -> float:
 
 
 # ------------------------------------------------------------------------------ oracle leg
+def fp32_vs_fp64_errors(f32_parts, f64_parts):
+    """Per-instance relative L2 errors of the FP32 result against FP64: of the field D and of
+    its power spectrum |D|^2."""
+    import numpy as np
+    field, power = [], []
+    for a, c in zip(f32_parts, f64_parts):
+        field.append(float(np.linalg.norm(a - c) / np.linalg.norm(c)))
+        pa, pc = np.abs(a) ** 2, np.abs(c) ** 2
+        power.append(float(np.linalg.norm(pa - pc) / np.linalg.norm(pc)))
+    return field, power
+
+
 def oracle_sample(target_s: float, sweep_index: int = 128, fixed_steps: int | None = None):
     """Time the FP64 direct-sum oracle on one instance of the sweep for a bounded number of
     RK4IP steps (about target_s seconds); returns (mode-steps/s, steps, seconds, field)."""
@@ -489,8 +501,7 @@ def run_gpu(args, world, rank, local):
         e1.synchronize()
         ms64 = e0.elapsed_time(e1)
         fin64 = b64.get_state()
-        errs = [float(np.linalg.norm(a - c) / np.linalg.norm(c))
-                for a, c in zip(b32.split(fin32), b64.split(fin64))]
+        errs, errs_p = fp32_vs_fp64_errors(b32.split(fin32), b64.split(fin64))
         # plain single-instance FP64 (N=64, 2000 steps)
         p = wl.plain64()
         bp = cme.Batch([cme.Instance.from_workload(p.instances[0])], precision=cme.FP64,
@@ -517,7 +528,9 @@ def run_gpu(args, world, rank, local):
             "fp32_speedup_vs_plain_fp64": value / world / (64 * p.nsteps / (min(tp) * 1e-3)),
         }
         error = {"fp32_vs_fp64_rel_l2_max": max(errs), "fp32_vs_fp64_rel_l2_median":
-                 statistics.median(errs), "instances": len(errs), "bound_fp32": 1e-4}
+                 statistics.median(errs), "instances": len(errs), "bound_fp32": 1e-4,
+                 "fp32_vs_fp64_spectrum_rel_l2_max": max(errs_p),
+                 "fp32_vs_fp64_spectrum_rel_l2_median": statistics.median(errs_p)}
 
     # end to end through the C ABI with host buffers
     pinned_in = torch.from_numpy(D0.view(np.float64).copy()).pin_memory()

@@ -30,3 +30,17 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_fp32_vs_fp64_error_helper():
+    """The helper behind the bench line's FP32-against-FP64 errors: relative L2 of the field
+    and of the power spectrum per instance."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    c = [np.array([1.0 + 0j, 2j]), np.array([3.0, 4.0 + 0j])]
+    a = [c[0] * (1 + 1e-6), c[1] + np.array([0.0, 1e-3])]
+    field, power = bench.fp32_vs_fp64_errors(a, c)
+    assert abs(field[0] - 1e-6) < 1e-12 and abs(field[1] - 1e-3 / 5.0) < 1e-12
+    assert abs(power[0] - ((1 + 1e-6) ** 2 - 1)) < 1e-12
+    assert abs(power[1] - abs(4.001 ** 2 - 16.0) / np.hypot(9.0, 16.0)) < 1e-12
