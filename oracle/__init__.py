@@ -66,9 +66,14 @@ def _configure(lib):
                                       c_double, c_double, c_double, c_long, dp, dp,
                                       c_double, dp]
     lib.oracle_fwm_vjp.argtypes = [c_int, c_int, c_int, dp, dp, dp]
+    lib.oracle_strang_grad.argtypes = [c_int, c_int, dp, dp, c_double, c_double, c_double,
+                                       c_double, c_double, c_double, c_long, dp, dp, c_double,
+                                       dp, dp, dp, dp, dp]
+    lib.oracle_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
+                                c_double, c_double, c_double, c_long, dp, dp, c_double, dp]
     for name in ("oracle_fwm", "oracle_rhs", "oracle_integrate", "oracle_integrate_eq1",
                  "oracle_dft", "oracle_invariants", "oracle_rk4ip_grad",
-                 "oracle_rk4ip_loss", "oracle_fwm_vjp"):
+                 "oracle_rk4ip_loss", "oracle_fwm_vjp", "oracle_strang_grad", "oracle_loss"):
         getattr(lib, name).restype = c_int
     return lib
 
@@ -188,25 +193,32 @@ def fwm_vjp(D, Wbar, linear: bool = False, M: int | None = None) -> np.ndarray:
 
 
 def log_spectrum_loss(inst, h: float, nsteps: int, target, eps: float = 1e-20,
-                      linear: bool = False, D0=None) -> float:
-    """L = sum_mu (log10(|D_mu|^2 + eps) - T_mu)^2 after nsteps RK4IP steps."""
+                      linear: bool = False, D0=None, method: int = RK4IP) -> float:
+    """L = sum_mu (log10(|D_mu|^2 + eps) - T_mu)^2 after nsteps RK4IP (or Strang) steps."""
     d = _cbuf(inst.D0 if D0 is None else D0)
     kap = np.ascontiguousarray(inst.kappa, dtype=np.float64)
     om = np.ascontiguousarray(inst.omega, dtype=np.float64)
     T = np.ascontiguousarray(target, dtype=np.float64)
     A = complex(inst.A_in)
     out = np.zeros(1)
-    _check(_load().oracle_rk4ip_loss(inst.N, int(linear), _modes(inst), _dp(kap), _dp(om), inst.g0,
-                                     inst.kappa_ext, A.real, A.imag, inst.sigma, h, int(nsteps),
-                                     _dp(d), _dp(T), eps, _dp(out)))
+    if method == RK4IP:
+        _check(_load().oracle_rk4ip_loss(inst.N, int(linear), _modes(inst), _dp(kap), _dp(om),
+                                         inst.g0, inst.kappa_ext, A.real, A.imag, inst.sigma, h,
+                                         int(nsteps), _dp(d), _dp(T), eps, _dp(out)))
+    else:
+        if method != STRANG or linear:
+            raise ValueError("loss: RK4IP (circular or linear) or Strang (circular)")
+        _check(_load().oracle_loss(1, inst.N, _modes(inst), _dp(kap), _dp(om), inst.g0,
+                                   inst.kappa_ext, A.real, A.imag, inst.sigma, h, int(nsteps),
+                                   _dp(d), _dp(T), eps, _dp(out)))
     return float(out[0])
 
 
 def log_spectrum_grad(inst, h: float, nsteps: int, target, eps: float = 1e-20,
-                      linear: bool = False):
-    """Discrete adjoint of the RK4IP run for the log-spectrum loss.  Returns a dict with the
-    loss and the gradients with respect to the initial field (complex, dL/dRe + i dL/dIm),
-    sigma, the omega_mu array, the kappa_mu array, A_in (complex) and, for
+                      linear: bool = False, method: int = RK4IP):
+    """Discrete adjoint of the RK4IP (or Strang) run for the log-spectrum loss.  Returns a dict
+    with the loss and the gradients with respect to the initial field (complex,
+    dL/dRe + i dL/dIm), sigma, the omega_mu array, the kappa_mu array, A_in (complex) and, for
     omega_mu = D2 mu^2/2 + D3 mu^3/6, D2 and D3."""
     N = inst.N
     d = _cbuf(inst.D0)
@@ -219,10 +231,18 @@ def log_spectrum_grad(inst, h: float, nsteps: int, target, eps: float = 1e-20,
     gLi = np.zeros(N)
     gLr = np.zeros(N)
     gP = np.zeros(2)
-    _check(_load().oracle_rk4ip_grad(N, int(linear), _modes(inst), _dp(kap), _dp(om), inst.g0,
-                                     inst.kappa_ext,
-                                     A.real, A.imag, inst.sigma, h, int(nsteps), _dp(d), _dp(T),
-                                     eps, _dp(loss), _dp(gD0), _dp(gLi), _dp(gLr), _dp(gP)))
+    if method == RK4IP:
+        _check(_load().oracle_rk4ip_grad(N, int(linear), _modes(inst), _dp(kap), _dp(om),
+                                         inst.g0, inst.kappa_ext, A.real, A.imag, inst.sigma, h,
+                                         int(nsteps), _dp(d), _dp(T), eps, _dp(loss), _dp(gD0),
+                                         _dp(gLi), _dp(gLr), _dp(gP)))
+    else:
+        if method != STRANG or linear:
+            raise ValueError("gradient: RK4IP (circular or linear) or Strang (circular)")
+        _check(_load().oracle_strang_grad(N, _modes(inst), _dp(kap), _dp(om), inst.g0,
+                                          inst.kappa_ext, A.real, A.imag, inst.sigma, h,
+                                          int(nsteps), _dp(d), _dp(T), eps, _dp(loss), _dp(gD0),
+                                          _dp(gLi), _dp(gLr), _dp(gP)))
     mu = np.arange(N) - N // 2
     # Im L_mu = omega_mu - omega_0 - sigma; Re L_mu = -kappa_mu / 2
     g_omega = gLi.copy()

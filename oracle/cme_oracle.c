@@ -635,6 +635,146 @@ int oracle_rk4ip_loss(int N, int linear, int M, const double* kappa, const doubl
     return rc;
 }
 
+/* ---------------------------------------------------------------------------------------
+ * Discrete adjoint of the Strang split step (reverse mode through exactly the sub-steps of
+ * step_strang), for the same log-power-spectrum loss and the same outputs as
+ * oracle_rk4ip_grad.  One step is
+ *     D1 = e D + c delta_{mu,0}             (exact linear + pump flow over dt = h/2,
+ *                                            e = exp(L dt), c = phi(L_0) p, phi(L) = (e^{L dt} - 1)/L)
+ *     a  = IDFT(D1),  b_j = a_j u_j,  u_j = exp(i g0 h |a_j|^2)     (exact Kerr flow)
+ *     D2 = m * DFT(b) / N                   (m: physical modes)
+ *     D3 = e D2 + c delta_{mu,0}.
+ * Reverse, with the cotangent convention of oracle_rk4ip_grad:
+ *   linear flow y = e x + c:   xbar = conj(e) ybar,  ebar += conj(x) ybar,  cbar += ybar_0;
+ *   D2 = m DFT(b)/N:           bbar = IDFT(m D2bar) / N   (the adjoint of DFT is IDFT);
+ *   b = a u(|a|^2), d b = u (1 + i g |a|^2) d a + i g a^2 u d conj(a):
+ *                              abar = conj(u) (1 - i g |a|^2) bbar + i g a^2 u conj(bbar);
+ *   a = IDFT(D1):              D1bar = DFT(abar);
+ *   e = exp(L dt):             Lbar += conj(dt e) ebar;
+ *   c = phi(L_0) p:            pbar = conj(phi(L_0)) cbar_total,
+ *                              Lbar_0 += conj(p phi'(L_0)) cbar_total,
+ *                              phi'(L) = (dt e^{L dt} - phi(L)) / L   (dt^2 / 2 at L = 0).
+ * ------------------------------------------------------------------------------------- */
+int oracle_strang_grad(int N, int M, const double* kappa, const double* omega, double g0,
+                       double kappa_ext, double ain_re, double ain_im, double sigma, double h,
+                       long nsteps, const double* D0, const double* target, double eps,
+                       double* loss, double* gD0, double* gLi, double* gLr, double* gP)
+{
+    if (check_model(N, kappa, omega) || !D0 || !target || nsteps < 0 || !loss || M < 1 || M > N)
+        return ORACLE_EINVAL;
+    model m = {N, 0, M, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    const double dt = 0.5 * h, gam = g0 * h;
+    cplx* traj = malloc(sizeof(cplx) * N * (size_t)(nsteps + 1));
+    cplx* w = malloc(sizeof(cplx) * 10 * N);
+    cplx *e = w, *D1 = w + N, *a = w + 2 * N, *u = w + 3 * N, *D2 = w + 4 * N,
+         *Db = w + 5 * N, *ab = w + 6 * N, *bb = w + 7 * N, *Eb = w + 8 * N, *tmp = w + 9 * N;
+    load(N, D0, traj);
+    for (int i = 0; i < N; ++i)   /* padding modes start at zero, whatever D0 holds there */
+        if (!physical(i, N, M))
+            traj[i] = 0.0;
+    for (long n = 0; n < nsteps; ++n) {
+        memcpy(traj + (size_t)(n + 1) * N, traj + (size_t)n * N, sizeof(cplx) * N);
+        step_strang(&m, h, traj + (size_t)(n + 1) * N, tmp);
+    }
+    /* loss and its seed */
+    const cplx* Df = traj + (size_t)nsteps * N;
+    double L = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double P = creal(Df[i]) * creal(Df[i]) + cimag(Df[i]) * cimag(Df[i]);
+        const double r = log10(P + eps) - target[i];
+        L += r * r;
+        const double dLdP = 2.0 * r / ((P + eps) * log(10.0));
+        Db[i] = 2.0 * dLdP * Df[i];
+    }
+    *loss = L;
+    const int c0 = N / 2;   /* centred index of the pumped mode mu = 0 */
+    const cplx p = sqrt(kappa_ext) * m.A_in;
+    for (int i = 0; i < N; ++i) {
+        e[i] = cexp(lin_coef(&m, i) * dt);
+        Eb[i] = 0.0;
+    }
+    const cplx L0 = lin_coef(&m, c0);
+    const cplx phi = cabs(L0) == 0.0 ? dt : (e[c0] - 1.0) / L0;
+    const cplx dphi = cabs(L0) == 0.0 ? 0.5 * dt * dt : (dt * e[c0] - phi) / L0;
+    cplx cbar = 0.0;
+    for (long n = nsteps - 1; n >= 0; --n) {
+        const cplx* D = traj + (size_t)n * N;
+        /* forward sub-steps of step n */
+        for (int i = 0; i < N; ++i)
+            D1[i] = e[i] * D[i];
+        D1[c0] += phi * p;
+        dft_modes_to_time(N, D1, a);
+        for (int j = 0; j < N; ++j) {
+            const double p2 = creal(a[j]) * creal(a[j]) + cimag(a[j]) * cimag(a[j]);
+            u[j] = cexp(I * (gam * p2));
+            tmp[j] = a[j] * u[j];
+        }
+        dft_time_to_modes(N, tmp, D2);
+        for (int i = 0; i < N; ++i)
+            D2[i] = physical(i, N, M) ? D2[i] / (double)N : 0.0;
+        /* reverse; Db holds the cotangent of D3 = e D2 + c */
+        cbar += Db[c0];
+        for (int i = 0; i < N; ++i) {
+            Eb[i] += conj(D2[i]) * Db[i];
+            Db[i] = conj(e[i]) * Db[i];                          /* D2bar */
+        }
+        for (int i = 0; i < N; ++i)
+            tmp[i] = physical(i, N, M) ? Db[i] : 0.0;
+        dft_modes_to_time(N, tmp, bb);                           /* N bbar */
+        for (int j = 0; j < N; ++j) {
+            bb[j] /= (double)N;
+            const double p2 = creal(a[j]) * creal(a[j]) + cimag(a[j]) * cimag(a[j]);
+            ab[j] = conj(u[j]) * (1.0 - I * gam * p2) * bb[j] +
+                    I * gam * a[j] * a[j] * u[j] * conj(bb[j]);
+        }
+        dft_time_to_modes(N, ab, D1);                            /* D1bar */
+        cbar += D1[c0];
+        for (int i = 0; i < N; ++i) {
+            Eb[i] += conj(D[i]) * D1[i];
+            Db[i] = conj(e[i]) * D1[i];                          /* Dbar of step n */
+        }
+    }
+    for (int i = 0; i < N; ++i) {
+        cplx Lb = conj(dt * e[i]) * Eb[i];
+        if (i == c0)
+            Lb += conj(p * dphi) * cbar;
+        gLr[i] = creal(Lb);
+        gLi[i] = cimag(Lb);
+    }
+    for (int i = 0; i < N; ++i)   /* D0 at the padding modes is overwritten by zero */
+        if (!physical(i, N, M))
+            Db[i] = 0.0;
+    store(N, Db, gD0);
+    const cplx pbar = conj(phi) * cbar;
+    gP[0] = creal(pbar);
+    gP[1] = cimag(pbar);
+    free(traj);
+    free(w);
+    return ORACLE_OK;
+}
+
+/* Loss of the forward run alone (for finite differences): method 0 = RK4IP, 1 = Strang. */
+int oracle_loss(int method, int N, int M, const double* kappa, const double* omega, double g0,
+                double kappa_ext, double ain_re, double ain_im, double sigma, double h,
+                long nsteps, const double* D0, const double* target, double eps, double* loss)
+{
+    if (check_model(N, kappa, omega) || !D0 || !target || !loss || (method != 0 && method != 1))
+        return ORACLE_EINVAL;
+    double* d = malloc(sizeof(double) * 2 * N);
+    memcpy(d, D0, sizeof(double) * 2 * N);
+    int rc = oracle_integrate(method, N, 0, M, kappa, omega, g0, kappa_ext, ain_re, ain_im, sigma,
+                              h, nsteps, d);
+    double L = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double P = d[2 * i] * d[2 * i] + d[2 * i + 1] * d[2 * i + 1];
+        const double r = log10(P + eps) - target[i];
+        L += r * r;
+    }
+    *loss = L;
+    free(d);
+    return rc;
+}
+
 /* J^H w for the FWM map at D (exposed for the dot-product test). */
 int oracle_fwm_vjp(int N, int linear, int M, const double* D, const double* Wbar, double* Dbar)
 {

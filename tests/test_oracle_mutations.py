@@ -74,6 +74,23 @@ MUTATIONS = {
     "adjoint: propagator cotangent": ("const cplx Lb = conj(0.5 * h * E[i]) * Eb[i];",
                                       "const cplx Lb = conj(h * E[i]) * Eb[i];"),
     "adjoint: pump cotangent conjugated": ("*pbar += ybar[N / 2];", "*pbar += conj(ybar[N / 2]);"),
+    # adjoint of the Strang split step
+    "Strang adjoint: phase factor not conjugated": (
+        "ab[j] = conj(u[j]) * (1.0 - I * gam * p2) * bb[j] +",
+        "ab[j] = u[j] * (1.0 - I * gam * p2) * bb[j] +"),
+    "Strang adjoint: sign of the |a|^2 term": ("(1.0 - I * gam * p2) * bb[j]",
+                                               "(1.0 + I * gam * p2) * bb[j]"),
+    "Strang adjoint: conjugate cotangent term": ("I * gam * a[j] * a[j] * u[j] * conj(bb[j]);",
+                                                 "I * gam * a[j] * a[j] * u[j] * bb[j];"),
+    "Strang adjoint: missing 1/N": ("bb[j] /= (double)N;", "bb[j] /= 1.0;"),
+    "Strang adjoint: pump cotangent of the second half flow": ("cbar += Db[c0];",
+                                                               "cbar += 0.0;"),
+    "Strang adjoint: derivative of the pump increment": ("(dt * e[c0] - phi) / L0",
+                                                         "(e[c0] - phi) / L0"),
+    "Strang adjoint: propagator cotangent over h": ("cplx Lb = conj(dt * e[i]) * Eb[i];",
+                                                    "cplx Lb = conj(h * e[i]) * Eb[i];"),
+    "Strang adjoint: padding modes in the Kerr cotangent": (
+        "tmp[i] = physical(i, N, M) ? Db[i] : 0.0;", "tmp[i] = Db[i];"),
 }
 
 
