@@ -138,6 +138,17 @@ int cme_set_field(cme_instance inst, const double* D0);
  * omega and field arrays keep N entries; padding entries are ignored.  Errors: INVALID_ARG. */
 int cme_set_modes(cme_instance inst, int M);
 
+/* Per-mode Kerr coefficients g0_mu (N values, centred, finite), or NULL to go back to g0 on
+ * every mode.  Sec. 2 notes that a constant g0 is no necessary restriction and that the
+ * coupled mode equations take frequency-dependent coefficients easily; the form implemented
+ * is the coefficient of the output mode,
+ *   dD_mu/dtau = L_mu D_mu + delta_{mu,0} sqrt(kappa_ext) A_in + i g0_mu FWM_mu(D),
+ * which keeps Eq. 4: a per-mode factor after the forward transform.  (A coefficient that
+ * depends on the whole quadruplet alpha, beta, gamma, mu has no transform form.)  RK4IP only:
+ * a batch with such an instance and the Strang integrator is refused, because the split step's
+ * exact Kerr flow needs one coefficient for all modes.  Errors: INVALID_ARG. */
+int cme_set_kerr(cme_instance inst, const double* g0_mu);
+
 void cme_destroy(cme_instance inst);
 
 /* ---- batches (device-resident sets of instances) --------------------------------------- */
@@ -219,9 +230,10 @@ int cme_debug_fault(cme_batch b, int what);
 
 /* Gradients of the log-power-spectrum misfit at the final step, per instance
  *     L = sum_mu (log10(|D_mu|^2 + eps) - T_mu)^2 ,
- * through nsteps RK4IP steps of size h (the paper's integrator, Sec. 2).  Every pointer is a
- * host array and may be NULL to skip that output; complex cotangents are dL/dRe + i dL/dIm,
- * interleaved; per-mode arrays are centred. */
+ * through nsteps steps of size h of the batch's integrator (Sec. 2: the RK4 method, RK4IP here,
+ * or the split-step Fourier method, the Strang split step here).  Every pointer is a host array
+ * and may be NULL to skip that output; complex cotangents are dL/dRe + i dL/dIm, interleaved;
+ * per-mode arrays are centred. */
 typedef struct cme_grads {
     double* loss;    /* [count] L of each instance */
     double* d_sigma; /* [count] dL/dsigma */
@@ -233,15 +245,21 @@ typedef struct cme_grads {
     double* d_D0;    /* [2*total_modes] cotangent of the field at the start of the call */
 } cme_grads;
 
-/* Run nsteps RK4IP steps from the current field with checkpoints every `segment` steps (0 =
- * ceil(sqrt(nsteps))), evaluate L against the target T (total_modes doubles: log10 powers,
- * centred, host memory), then run the discrete adjoint backwards, recomputing each segment from
- * its checkpoint (the recomputation of the next segment overlaps the backward pass of the
- * current one, on a second stream).  The batch ends at the final field (tau advanced by
+/* Run nsteps steps of the batch's integrator from the current field with checkpoints every
+ * `segment` steps (0 = ceil(sqrt(nsteps))), evaluate L against the target T (total_modes
+ * doubles: log10 powers, centred, host memory), then run the discrete adjoint backwards,
+ * recomputing each segment from its checkpoint (the recomputation of the next segment overlaps
+ * the backward pass of the current one, on a second stream).  RK4IP: per step the state, the
+ * three stage values and the time-domain fields of the four stage inputs are recomputed, and
+ * the backward pass runs four vector-Jacobian products of the right-hand side.  Strang: the
+ * state, the time-domain field of the Kerr flow and the state after it are recomputed, and the
+ * backward pass runs the exact Kerr flow's vector-Jacobian product (two transforms) between the
+ * two linear half flows; the pump increment (exp(L_0 h/2) - 1)/L_0 sqrt(kappa_ext) A_in passes
+ * its cotangent to A_in and to L_0.  The batch ends at the final field (tau advanced by
  * h nsteps).  Scratch memory -- ceil(nsteps/segment) checkpoints and the states plus stage
  * values of two segments, 8 * segment field vectors -- is allocated on the first call and kept
- * with the batch.  RK4IP batches only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM,
- * TIMEOUT (a bounded wait of a cluster all-to-all gave up). */
+ * with the batch.  N <= 4096 only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM, TIMEOUT (a
+ * bounded wait of a cluster all-to-all gave up). */
 int cme_grad(cme_batch b, double h, long nsteps, const double* target, double eps, long segment,
              cme_grads* out);
 
@@ -268,9 +286,13 @@ int cme_eval_rhs(cme_batch b, double* out, int where);
  * cudaMalloc, which can synchronise the whole device, must not be called.
  *
  * Advances `count` instances of N modes (power of two in [4, 4096]) by nsteps RK4IP steps of
- * size h in FP64, in place, with the same kernels as cme_step on an FP64 RK4IP batch, and
- * calls no cudaMalloc, cudaFree or allocating library routine.  All pointers are device memory
- * owned by the caller:
+ * size h in FP64, in place, and calls no cudaMalloc, cudaFree or allocating library routine.
+ * It runs the one-block step kernels of cme_step with the launch shape (values per thread,
+ * instances per block) that cme_batch_create chooses for an FP64 RK4IP batch of these
+ * instances under default options before its choice of thread-block clusters: the result is
+ * bit for bit that of such a batch created with cluster = 1.  Where the default batch spreads
+ * N = 2048 or 4096 instances over clusters, the two agree to rounding only.  All pointers are
+ * device memory owned by the caller:
  *   d_kappa, d_omega  N * count doubles each: kappa_mu and omega_mu per instance, centred;
  *   d_inst            5 * count doubles: (g0, kappa_ext, Re A_in, Im A_in, sigma) per instance;
  *   d_field           2 * N * count doubles (in/out): rotating-frame field, interleaved, centred.
@@ -281,8 +303,13 @@ int cme_eval_rhs(cme_batch b, double* out, int where);
  * CME_ERR_INVALID_ARG.  Every call shares that array and it keeps the previous call's
  * contents (the status words are cleared by each call): calls that overlap on the GPU, on
  * different streams or from different threads, race and corrupt each other.  The first call on
- * a device takes the array's device address with cudaGetSymbolAddress; make that first call
- * before any stream capture.  Errors: UNSUPPORTED_N, INVALID_ARG, CUDA. */
+ * a device takes the array's device address with cudaGetSymbolAddress and keeps it; make that
+ * first call before any stream capture, and do not call this entry point again on a device
+ * after cudaDeviceReset (the kept address belongs to the context that was reset).  Non-finite
+ * results are not reported: the call returns before the kernels run and reads nothing back,
+ * so a field that overflows to Inf or NaN comes back in d_field with CME_OK; check d_field.
+ * Six kernels per call (five when nsteps = 0) count towards cme_kernel_launches.
+ * Errors: UNSUPPORTED_N, INVALID_ARG, CUDA. */
 int cme_rk4ip_noalloc(int N, int count, double h, long nsteps, const double* d_kappa,
                       const double* d_omega, const double* d_inst, double* d_field,
                       void* cuda_stream);

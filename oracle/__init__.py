@@ -50,26 +50,26 @@ def _configure(lib):
     dp = ctypes.POINTER(ctypes.c_double)
     c_int, c_long, c_double = ctypes.c_int, ctypes.c_long, ctypes.c_double
     lib.oracle_fwm.argtypes = [c_int, c_int, c_int, dp, dp]
-    lib.oracle_rhs.argtypes = [c_int, c_int, c_int, c_double, c_double, c_double, c_double,
+    lib.oracle_rhs.argtypes = [c_int, c_int, c_int, c_double, dp, c_double, c_double, c_double,
                                dp, dp]
-    lib.oracle_integrate.argtypes = [c_int, c_int, c_int, c_int, dp, dp, c_double, c_double,
+    lib.oracle_integrate.argtypes = [c_int, c_int, c_int, c_int, dp, dp, c_double, dp, c_double,
                                      c_double, c_double, c_double, c_double, c_long, dp]
     lib.oracle_integrate_eq1.argtypes = [c_int, c_int, dp, dp, c_double, c_double,
                                          c_double, c_double, c_double, c_double,
                                          c_double, c_long, dp]
     lib.oracle_dft.argtypes = [c_int, c_int, dp, dp]
     lib.oracle_invariants.argtypes = [c_int, c_int, dp, c_double, c_double, dp, dp]
-    lib.oracle_rk4ip_grad.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
-                                      c_double, c_double, c_double, c_long, dp, dp,
+    lib.oracle_rk4ip_grad.argtypes = [c_int, c_int, c_int, dp, dp, c_double, dp, c_double,
+                                      c_double, c_double, c_double, c_double, c_long, dp, dp,
                                       c_double, dp, dp, dp, dp, dp]
-    lib.oracle_rk4ip_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
-                                      c_double, c_double, c_double, c_long, dp, dp,
+    lib.oracle_rk4ip_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, dp, c_double,
+                                      c_double, c_double, c_double, c_double, c_long, dp, dp,
                                       c_double, dp]
     lib.oracle_fwm_vjp.argtypes = [c_int, c_int, c_int, dp, dp, dp]
     lib.oracle_strang_grad.argtypes = [c_int, c_int, dp, dp, c_double, c_double, c_double,
                                        c_double, c_double, c_double, c_long, dp, dp, c_double,
                                        dp, dp, dp, dp, dp]
-    lib.oracle_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, c_double, c_double,
+    lib.oracle_loss.argtypes = [c_int, c_int, c_int, dp, dp, c_double, dp, c_double, c_double,
                                 c_double, c_double, c_double, c_long, dp, dp, c_double, dp]
     for name in ("oracle_fwm", "oracle_rhs", "oracle_integrate", "oracle_integrate_eq1",
                  "oracle_dft", "oracle_invariants", "oracle_rk4ip_grad",
@@ -102,6 +102,18 @@ def _modes(inst) -> int:
     return int(M) if M else int(inst.N)
 
 
+def _kerr(inst):
+    """Per-mode Kerr coefficients g0_mu of an instance (centred, float64), or None: the
+    instance's g0 on every mode."""
+    g = getattr(inst, "g0_mu", None)
+    return None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+
+
+def _dpo(a):
+    """Pointer to a float64 array, or NULL for None."""
+    return None if a is None else _dp(a)
+
+
 def _cbuf(z) -> np.ndarray:
     z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
     return np.ascontiguousarray(z.view(np.float64).copy())
@@ -127,13 +139,15 @@ def fwm(D, linear: bool = False, M: int | None = None) -> np.ndarray:
 
 
 def rhs(D, g0: float, kappa_ext: float, A_in: complex, linear: bool = False,
-        M: int | None = None) -> np.ndarray:
-    """F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D)."""
+        M: int | None = None, g0_mu=None) -> np.ndarray:
+    """F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D); with g0_mu (N values, centred)
+    the Kerr coefficient of output mode mu is g0_mu[mu] instead of g0."""
     d = _cbuf(D)
     N = d.size // 2
     out = np.empty_like(d)
-    _check(_load().oracle_rhs(N, int(linear), int(M or N), g0, kappa_ext, complex(A_in).real,
-                              complex(A_in).imag, _dp(d), _dp(out)))
+    g = None if g0_mu is None else np.ascontiguousarray(g0_mu, dtype=np.float64)
+    _check(_load().oracle_rhs(N, int(linear), int(M or N), g0, _dpo(g), kappa_ext,
+                              complex(A_in).real, complex(A_in).imag, _dp(d), _dp(out)))
     return out.view(np.complex128)
 
 
@@ -145,9 +159,10 @@ def integrate(inst, h: float, nsteps: int, method: int = RK4IP, linear: bool = F
     kap = np.ascontiguousarray(inst.kappa, dtype=np.float64)
     om = np.ascontiguousarray(inst.omega, dtype=np.float64)
     A = complex(inst.A_in)
+    g = _kerr(inst)
     _check(_load().oracle_integrate(method, inst.N, int(linear), _modes(inst), _dp(kap), _dp(om),
-                                    inst.g0, inst.kappa_ext, A.real, A.imag, inst.sigma, h,
-                                    int(nsteps), _dp(d)))
+                                    inst.g0, _dpo(g), inst.kappa_ext, A.real, A.imag, inst.sigma,
+                                    h, int(nsteps), _dp(d)))
     return d.view(np.complex128)
 
 
@@ -201,14 +216,16 @@ def log_spectrum_loss(inst, h: float, nsteps: int, target, eps: float = 1e-20,
     T = np.ascontiguousarray(target, dtype=np.float64)
     A = complex(inst.A_in)
     out = np.zeros(1)
+    g = _kerr(inst)
     if method == RK4IP:
         _check(_load().oracle_rk4ip_loss(inst.N, int(linear), _modes(inst), _dp(kap), _dp(om),
-                                         inst.g0, inst.kappa_ext, A.real, A.imag, inst.sigma, h,
-                                         int(nsteps), _dp(d), _dp(T), eps, _dp(out)))
+                                         inst.g0, _dpo(g), inst.kappa_ext, A.real, A.imag,
+                                         inst.sigma, h, int(nsteps), _dp(d), _dp(T), eps,
+                                         _dp(out)))
     else:
         if method != STRANG or linear:
             raise ValueError("loss: RK4IP (circular or linear) or Strang (circular)")
-        _check(_load().oracle_loss(1, inst.N, _modes(inst), _dp(kap), _dp(om), inst.g0,
+        _check(_load().oracle_loss(1, inst.N, _modes(inst), _dp(kap), _dp(om), inst.g0, _dpo(g),
                                    inst.kappa_ext, A.real, A.imag, inst.sigma, h, int(nsteps),
                                    _dp(d), _dp(T), eps, _dp(out)))
     return float(out[0])
@@ -233,12 +250,14 @@ def log_spectrum_grad(inst, h: float, nsteps: int, target, eps: float = 1e-20,
     gP = np.zeros(2)
     if method == RK4IP:
         _check(_load().oracle_rk4ip_grad(N, int(linear), _modes(inst), _dp(kap), _dp(om),
-                                         inst.g0, inst.kappa_ext, A.real, A.imag, inst.sigma, h,
+                                         inst.g0, _dpo(_kerr(inst)), inst.kappa_ext, A.real,
+                                         A.imag, inst.sigma, h,
                                          int(nsteps), _dp(d), _dp(T), eps, _dp(loss), _dp(gD0),
                                          _dp(gLi), _dp(gLr), _dp(gP)))
     else:
-        if method != STRANG or linear:
-            raise ValueError("gradient: RK4IP (circular or linear) or Strang (circular)")
+        if method != STRANG or linear or _kerr(inst) is not None:
+            raise ValueError("gradient: RK4IP (circular or linear), or Strang (circular, "
+                             "constant g0)")
         _check(_load().oracle_strang_grad(N, _modes(inst), _dp(kap), _dp(om), inst.g0,
                                           inst.kappa_ext, A.real, A.imag, inst.sigma, h,
                                           int(nsteps), _dp(d), _dp(T), eps, _dp(loss), _dp(gD0),

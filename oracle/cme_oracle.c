@@ -19,6 +19,8 @@
  *     dD_mu/dtau = L_mu D_mu + F_mu(D),
  *     L_mu = -kappa_mu/2 + i (omega_mu - omega_0 - sigma),
  *     F_mu(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM_mu(D),
+ *     (optionally a per-mode g0_mu in place of g0: a frequency-dependent Kerr coefficient of
+ *     the output mode, Sec. 2 noting that a constant g0 is no necessary restriction),
  *     FWM_mu(D) = sum_{alpha - beta + gamma = mu} D_alpha conj(D_beta) D_gamma.
  * The constraint alpha - beta + gamma = mu is taken modulo N ("circular", the reading that
  * matches Eq. 4 with an N-point transform) or literally ("linear", no wrap-around).
@@ -115,14 +117,21 @@ typedef struct {
     double kappa_ext;
     cplx A_in;
     double sigma;
+    const double* g0mu;   /* per-mode Kerr coefficients g0_mu (centred), or NULL: g0 on every mode */
 } model;
 
-/* F(D) = pump + i g0 FWM(D) */
+/* Kerr coefficient of the four-wave-mixing term of output mode i (centred index). */
+static double kerr_coef(const model* m, int i)
+{
+    return m->g0mu ? m->g0mu[i] : m->g0;
+}
+
+/* F(D) = pump + i g0 FWM(D); with per-mode coefficients F_mu = pump + i g0_mu FWM_mu(D) */
 static void rhs_nonlinear(const model* m, const cplx* D, cplx* out)
 {
     fwm_direct(m->N, m->linear, m->M, D, out);
     for (int i = 0; i < m->N; ++i)
-        out[i] *= I * m->g0;
+        out[i] *= I * kerr_coef(m, i);
     out[m->N / 2] += sqrt(m->kappa_ext) * m->A_in;
 }
 
@@ -274,13 +283,13 @@ int oracle_fwm(int N, int linear, int M, const double* D, double* out)
     return ORACLE_OK;
 }
 
-/* F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D) */
-int oracle_rhs(int N, int linear, int M, double g0, double kappa_ext, double ain_re,
-               double ain_im, const double* D, double* out)
+/* F(D) = delta_{mu,0} sqrt(kappa_ext) A_in + i g0 FWM(D) (g0mu: per-mode g0_mu, or NULL) */
+int oracle_rhs(int N, int linear, int M, double g0, const double* g0mu, double kappa_ext,
+               double ain_re, double ain_im, const double* D, double* out)
 {
     if (N < 1 || M < 1 || M > N || !D || !out)
         return ORACLE_EINVAL;
-    model m = {N, linear, M, NULL, NULL, g0, kappa_ext, ain_re + I * ain_im, 0.0};
+    model m = {N, linear, M, NULL, NULL, g0, kappa_ext, ain_re + I * ain_im, 0.0, g0mu};
     cplx* d = malloc(sizeof(cplx) * 2 * N);
     load(N, D, d);
     rhs_nonlinear(&m, d, d + N);
@@ -289,17 +298,20 @@ int oracle_rhs(int N, int linear, int M, double g0, double kappa_ext, double ain
     return ORACLE_OK;
 }
 
-/* method: 0 = RK4IP, 1 = Strang, 2 = plain RK4.  D (2N doubles) is advanced in place. */
+/* method: 0 = RK4IP, 1 = Strang, 2 = plain RK4.  D (2N doubles) is advanced in place.
+ * g0mu: per-mode Kerr coefficients (N, centred) or NULL; the Strang step has no exact Kerr flow
+ * with per-mode coefficients and refuses them. */
 int oracle_integrate(int method, int N, int linear, int M, const double* kappa,
-                     const double* omega, double g0, double kappa_ext, double ain_re,
-                     double ain_im, double sigma, double h, long nsteps, double* D)
+                     const double* omega, double g0, const double* g0mu, double kappa_ext,
+                     double ain_re, double ain_im, double sigma, double h, long nsteps,
+                     double* D)
 {
     if (check_model(N, kappa, omega) || !D || nsteps < 0 || method < 0 || method > 2 || M < 1 ||
         M > N)
         return ORACLE_EINVAL;
-    if (method == 1 && linear)
+    if (method == 1 && (linear || g0mu))
         return ORACLE_EINVAL;
-    model m = {N, linear, M, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    model m = {N, linear, M, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma, g0mu};
     cplx* d = malloc(sizeof(cplx) * N);
     cplx* w = malloc(sizeof(cplx) * 8 * N);
     load(N, D, d);
@@ -488,13 +500,13 @@ static void fwm_vjp(int N, int linear, int M, const cplx* D, const cplx* Wbar, c
     }
 }
 
-/* xbar += J_F(x)^H ybar for F(x) = pump + i g0 FWM(x); pbar += ybar at mu = 0. */
+/* xbar += J_F(x)^H ybar for F(x) = pump + i g0_mu FWM(x); pbar += ybar at mu = 0. */
 static void rhs_vjp(const model* m, const cplx* x, const cplx* ybar, cplx* xbar, cplx* pbar,
                     cplx* tmp)
 {
     const int N = m->N;
     for (int i = 0; i < N; ++i)
-        tmp[i] = conj(I * m->g0) * ybar[i];
+        tmp[i] = conj(I * kerr_coef(m, i)) * ybar[i];
     fwm_vjp(N, m->linear, m->M, x, tmp, tmp + N);
     for (int i = 0; i < N; ++i)
         xbar[i] += tmp[N + i];
@@ -502,13 +514,14 @@ static void rhs_vjp(const model* m, const cplx* x, const cplx* ybar, cplx* xbar,
 }
 
 int oracle_rk4ip_grad(int N, int linear, int M, const double* kappa, const double* omega,
-                      double g0, double kappa_ext, double ain_re, double ain_im, double sigma,
-                      double h, long nsteps, const double* D0, const double* target, double eps,
-                      double* loss, double* gD0, double* gLi, double* gLr, double* gP)
+                      double g0, const double* g0mu, double kappa_ext, double ain_re,
+                      double ain_im, double sigma, double h, long nsteps, const double* D0,
+                      const double* target, double eps, double* loss, double* gD0, double* gLi,
+                      double* gLr, double* gP)
 {
     if (check_model(N, kappa, omega) || !D0 || !target || nsteps < 0 || !loss || M < 1 || M > N)
         return ORACLE_EINVAL;
-    model m = {N, linear, M, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma};
+    model m = {N, linear, M, kappa, omega, g0, kappa_ext, ain_re + I * ain_im, sigma, g0mu};
     cplx* traj = malloc(sizeof(cplx) * N * (size_t)(nsteps + 1));
     cplx* w = malloc(sizeof(cplx) * 24 * N);
     cplx *E = w, *y1 = w + N, *k1 = w + 2 * N, *k2 = w + 3 * N, *k3 = w + 4 * N,
@@ -614,7 +627,8 @@ int oracle_rk4ip_grad(int N, int linear, int M, const double* kappa, const doubl
 
 /* Loss of the forward RK4IP run alone (for finite differences). */
 int oracle_rk4ip_loss(int N, int linear, int M, const double* kappa, const double* omega,
-                      double g0, double kappa_ext, double ain_re, double ain_im, double sigma,
+                      double g0, const double* g0mu, double kappa_ext, double ain_re,
+                      double ain_im, double sigma,
                       double h, long nsteps, const double* D0, const double* target, double eps,
                       double* loss)
 {
@@ -622,7 +636,8 @@ int oracle_rk4ip_loss(int N, int linear, int M, const double* kappa, const doubl
         return ORACLE_EINVAL;
     double* d = malloc(sizeof(double) * 2 * N);
     memcpy(d, D0, sizeof(double) * 2 * N);
-    int rc = oracle_integrate(0, N, linear, M, kappa, omega, g0, kappa_ext, ain_re, ain_im, sigma,
+    int rc = oracle_integrate(0, N, linear, M, kappa, omega, g0, g0mu, kappa_ext, ain_re, ain_im,
+                              sigma,
                               h, nsteps, d);
     double L = 0.0;
     for (int i = 0; i < N; ++i) {
@@ -755,14 +770,16 @@ int oracle_strang_grad(int N, int M, const double* kappa, const double* omega, d
 
 /* Loss of the forward run alone (for finite differences): method 0 = RK4IP, 1 = Strang. */
 int oracle_loss(int method, int N, int M, const double* kappa, const double* omega, double g0,
-                double kappa_ext, double ain_re, double ain_im, double sigma, double h,
+                const double* g0mu, double kappa_ext, double ain_re, double ain_im, double sigma,
+                double h,
                 long nsteps, const double* D0, const double* target, double eps, double* loss)
 {
     if (check_model(N, kappa, omega) || !D0 || !target || !loss || (method != 0 && method != 1))
         return ORACLE_EINVAL;
     double* d = malloc(sizeof(double) * 2 * N);
     memcpy(d, D0, sizeof(double) * 2 * N);
-    int rc = oracle_integrate(method, N, 0, M, kappa, omega, g0, kappa_ext, ain_re, ain_im, sigma,
+    int rc = oracle_integrate(method, N, 0, M, kappa, omega, g0, g0mu, kappa_ext, ain_re, ain_im,
+                              sigma,
                               h, nsteps, d);
     double L = 0.0;
     for (int i = 0; i < N; ++i) {

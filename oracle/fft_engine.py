@@ -58,7 +58,10 @@ class Batch:
                               for i in instances])
         self.kappa = np.stack([np.asarray(i.kappa, dtype=np.float64) for i in instances])
         self.omega = np.stack([np.asarray(i.omega, dtype=np.float64) for i in instances])
-        self.g0 = np.array([i.g0 for i in instances])[:, None]
+        # Kerr coefficient of each output mode: g0, or the instance's per-mode g0_mu
+        self.g0 = np.stack([np.full(self.N, float(i.g0)) if getattr(i, "g0_mu", None) is None
+                            else np.asarray(i.g0_mu, dtype=np.float64) for i in instances])
+        self.kerr_per_mode = any(getattr(i, "g0_mu", None) is not None for i in instances)
         self.pump = np.array([np.sqrt(i.kappa_ext) * complex(i.A_in) for i in instances])
         self.sigma = np.array([i.sigma for i in instances])[:, None]
         om0 = self.omega[:, self.N // 2][:, None]
@@ -91,6 +94,8 @@ def strang(batch: Batch, h: float, nsteps: int, D=None):
     """Strang split step: exact linear+pump half step, exact Kerr phase rotation of the
     time-domain field a (da/dtau = i g0 |a|^2 a) followed by zeroing the padding modes, exact
     linear+pump half step."""
+    if batch.kerr_per_mode:
+        raise ValueError("the Strang step has no exact Kerr flow with per-mode coefficients")
     D = np.where(batch.mask, batch.D0 if D is None else np.asarray(D), 0.0).astype(np.complex128)
     N = batch.N
     e = np.exp(batch.L * (0.5 * h))
@@ -101,8 +106,15 @@ def strang(batch: Batch, h: float, nsteps: int, D=None):
         D = e * D
         D[:, N // 2] += c0
         a = np.fft.ifft(_to_fft(D), axis=-1) * N
-        a = a * np.exp(1j * batch.g0 * np.abs(a) ** 2 * h)
+        a = a * np.exp(1j * batch.g0[:, :1] * np.abs(a) ** 2 * h)
         D = np.where(batch.mask, _to_centred(np.fft.fft(a, axis=-1) / N), 0.0)
         D = e * D
         D[:, N // 2] += c0
     return D
+
+
+def rk4ip_one(job):
+    """One instance's RK4IP run, job = (instance, h, nsteps): the unit of work the tests hand
+    to a spawn process pool when many long single-instance runs are needed."""
+    inst, h, nsteps = job
+    return rk4ip(Batch([inst]), h, nsteps)[0]

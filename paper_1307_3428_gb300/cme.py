@@ -68,6 +68,7 @@ _SIGS = [
                                       ctypes.c_double, ctypes.POINTER(_VP)]),
     ("cme_set_field", ctypes.c_int, [_VP, _DP]),
     ("cme_set_modes", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("cme_set_kerr", ctypes.c_int, [_VP, _DP]),
     ("cme_destroy", None, [_VP]),
     ("cme_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int,
                                         ctypes.POINTER(Options), _VP, ctypes.POINTER(_VP)]),
@@ -162,7 +163,8 @@ def use_torch_allocator():
 class Instance:
     """Host-side parameters of one CME problem (see cme_create)."""
 
-    def __init__(self, N, kappa, omega, g0, kappa_ext, A_in, sigma, D0=None, M=None):
+    def __init__(self, N, kappa, omega, g0, kappa_ext, A_in, sigma, D0=None, M=None,
+                 g0_mu=None):
         lib = load()
         kap = np.ascontiguousarray(kappa, dtype=np.float64)
         om = np.ascontiguousarray(omega, dtype=np.float64)
@@ -176,6 +178,8 @@ class Instance:
             self.set_field(D0)
         if M is not None:
             self.set_modes(M)
+        if g0_mu is not None:
+            self.set_kerr(g0_mu)
 
     @classmethod
     def from_eq2(cls, N, Omega, f0, kappa_rel=None, D0=None, M=None) -> "Instance":
@@ -198,11 +202,20 @@ class Instance:
     @classmethod
     def from_workload(cls, inst) -> "Instance":
         return cls(inst.N, inst.kappa, inst.omega, inst.g0, inst.kappa_ext, inst.A_in,
-                   inst.sigma, inst.D0, getattr(inst, "M", None))
+                   inst.sigma, inst.D0, getattr(inst, "M", None), getattr(inst, "g0_mu", None))
 
     def set_modes(self, M: int):
         """Physical mode count (cme_set_modes): the centred M of the N modes."""
         _check(load().cme_set_modes(self.handle, int(M)))
+
+    def set_kerr(self, g0_mu):
+        """Per-mode Kerr coefficients g0_mu (cme_set_kerr; centred); None restores g0."""
+        if g0_mu is None:
+            _check(load().cme_set_kerr(self.handle, None))
+        else:
+            g = np.ascontiguousarray(g0_mu, dtype=np.float64)
+            assert g.size == self.N
+            _check(load().cme_set_kerr(self.handle, _dptr(g)))
 
     def set_field(self, D0):
         d = _interleave(D0)
@@ -334,8 +347,9 @@ class Batch:
         return out.view(np.complex128)
 
     def grad(self, h: float, nsteps: int, target, eps: float = 1e-20, segment: int = 0) -> dict:
-        """cme_grad: loss and gradients of the log-power-spectrum misfit after nsteps RK4IP
-        steps from the current field (the batch ends at the final field)."""
+        """cme_grad: loss and gradients of the log-power-spectrum misfit after nsteps steps of
+        the batch's integrator (RK4IP or Strang) from the current field (the batch ends at the
+        final field)."""
         T = np.ascontiguousarray(target, dtype=np.float64).reshape(-1)
         assert T.size == self.total
         C, M = self.count, self.total

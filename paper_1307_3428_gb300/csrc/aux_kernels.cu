@@ -75,6 +75,36 @@ __global__ void prop_kernel(PropArgs a)
             c = make_double2(qr * p.x - qi * p.y, qr * p.y + qi * p.x);
         }
         a.cpump[i] = c;
+        if (a.cphi) {
+            // phi(L) = (exp(L hh) - 1)/L and phi'(L) = (hh exp(L hh) - phi(L))/L; for small
+            // |z| = |L hh| the series phi'(L) = hh^2 sum_{k>=1} k z^(k-1)/(k+1)! (12 terms,
+            // truncation below 1e-20 at |z| < 0.1) avoids the cancellation of the quotient
+            const double zr = Lr * hh, zi = Li * hh;
+            double2 phi, dphi;
+            if (den == 0.0)
+                phi = make_double2(hh, 0.0);
+            else
+                phi = make_double2((e1.x * Lr + e1.y * Li) / den, (e1.y * Lr - e1.x * Li) / den);
+            if (zr * zr + zi * zi < 0.01) {
+                double sr = 0.0, si = 0.0;   // Horner in z over k = 12 .. 1
+                double fact = 1.0;           // (k+1)! for k = 12
+                for (int k = 2; k <= 13; ++k)
+                    fact *= k;
+                for (int k = 12; k >= 1; --k) {
+                    const double ck = (double)k / fact;
+                    const double tr = sr * zr - si * zi + ck, ti = sr * zi + si * zr;
+                    sr = tr;
+                    si = ti;
+                    fact /= (double)(k + 1);
+                }
+                dphi = make_double2(hh * hh * sr, hh * hh * si);
+            } else {
+                const double nr = hh * (e1.x + 1.0) - phi.x, ni = hh * e1.y - phi.y;
+                dphi = make_double2((nr * Lr + ni * Li) / den, (ni * Lr - nr * Li) / den);
+            }
+            a.cphi[2 * i] = phi;
+            a.cphi[2 * i + 1] = dphi;
+        }
     }
 }
 
@@ -230,6 +260,24 @@ __global__ void loss_seed_kernel(int prec, int total, const int* mode_inst, cons
         reinterpret_cast<float2*>(dbar)[m] = make_float2((float)(g * v.x), (float)(g * v.y));
 }
 
+__global__ void strang_pump_grad_kernel(int count, const long long* inst_off,
+                                        const double2* cphi, const double2* pump, double2* pbar,
+                                        double2* gL)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count)
+        return;
+    const double2 cb = pbar[i], phi = cphi[2 * i], dphi = cphi[2 * i + 1], p = pump[i];
+    // conj(phi) cbar
+    pbar[i] = make_double2(phi.x * cb.x + phi.y * cb.y, phi.x * cb.y - phi.y * cb.x);
+    // conj(p phi') cbar, added at the pumped mode (transform position 0 of the instance)
+    const double qr = p.x * dphi.x - p.y * dphi.y, qi = p.x * dphi.y + p.y * dphi.x;
+    double2 g = gL[inst_off[i]];
+    g.x += qr * cb.x + qi * cb.y;
+    g.y += qr * cb.y - qi * cb.x;
+    gL[inst_off[i]] = g;
+}
+
 __global__ void grad_reduce_kernel(const int* inst_N, const long long* inst_off, const double2* gL,
                                    const double* loss_modes, double* red)
 {
@@ -347,6 +395,15 @@ cudaError_t launch_loss_seed(int prec, int total, const int* mode_inst, const in
 {
     loss_seed_kernel<<<nblocks(total, 256), 256, 0, s>>>(prec, total, mode_inst, inst_N, inst_off,
                                                           hi, lo, target, eps, loss, dbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strang_pump_grad(int count, const long long* inst_off, const double2* cphi,
+                                    const double2* pump, double2* pbar, double2* gL,
+                                    cudaStream_t s)
+{
+    strang_pump_grad_kernel<<<nblocks(count, 128), 128, 0, s>>>(count, inst_off, cphi, pump,
+                                                                 pbar, gL);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ CME_DEV int adj_setup(Group<T, LOGN, R, C>& grp, unsigned char* smem, const Step
     }
     if (a.phys)
         grp.set_modes(a.phys[inst]);
+    grp.set_kerr(a.kerr, a.base + (long long)inst * Group<T, LOGN, R, C>::N);
     return inst;
 }
 
@@ -124,10 +125,11 @@ CME_HD constexpr size_t adj_backward_smem()
            (adj_prefetch<T, LOGN, R, C>() ? adj_prefetch_bytes<T, LOGN, R, C>() + 16 : 0);
 }
 
-// Recompute role: the states of segment A.seg from its checkpoint, the stage values y1, k2, k3
-// and the time-domain fields of the four stage inputs of every step, into half (A.seg mod 2)
-// of A.stages.
-template <typename T, int LOGN, int R, int C = 1>
+// Recompute role: the states of segment A.seg from its checkpoint and, for every step, into
+// half (A.seg mod 2) of A.stages: RK4IP, the stage values y1, k2, k3 and the time-domain fields
+// of the four stage inputs; Strang, the time-domain field of the Kerr flow and the state after
+// it.
+template <typename T, int LOGN, int R, int C = 1, int METHOD = METHOD_RK4IP>
 __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(const AdjArgs A)
 {
     using GR = Group<T, LOGN, R, C>;
@@ -162,7 +164,10 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
             for (int j = 0; j < R; ++j)
                 o[j * P] = fs.Dh[j];
         }
-        rk4ip_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
+        if constexpr (METHOD == METHOD_RK4IP)
+            rk4ip_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
+        else
+            strang_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
     }
     if (grp.failed() && a.status)
         a.status[inst] = 2;
@@ -295,7 +300,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 z[j] = {gNn * cot[j].im, -gNn * cot[j].re};
-            grp.mask(z);   // F is zero on padding modes: their cotangent does not enter
+            grp.out_modes(z);   // the per-mode Kerr factor; F is zero on padding modes,
+                                // whose cotangent does not enter
 #pragma unroll 1
             for (int p = 0; p < 2; ++p) {
                 if (p == 1) {
@@ -356,6 +362,136 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
             A.pbar[inst] = pb;
     }
     if ((grp.failed() || pf_failed) && a.status)
+        a.status[inst] = 2;
+    if constexpr (C > 1)
+        cluster_sync();   // no block leaves while a peer may still address its shared memory
+}
+
+// Backward role of the Strang split step (Sec. 2, split-step Fourier method with the field in
+// the frequency domain): the discrete adjoint of the steps of segment A.seg, last step first,
+// from the states D, the time-domain fields a of the Kerr flow and the states D2 after it in
+// half (A.seg mod 2) of A.stages.  One step of the forward kernels is
+//     D1 = E D + c,  a = IDFT(D1),  D2 = D1 + m DFT(a (u - 1)) / N,  D3 = E D2 + c,
+// with E = exp(L h/2), c the pump increment of the linear half flow on mu = 0,
+// u = exp(i g0 h |a|^2) and m the physical modes.  In reverse:
+//     D2bar = conj(E) D3bar,            Lbar += conj(h/2 E) conj(D2) D3bar,  cbar += D3bar_0;
+//     bbar = IDFT(m D2bar) / N,
+//     abar = (conj(u) (1 - i g0 h |a|^2) - 1) bbar + i g0 h a^2 u conj(bbar),
+//     D1bar = D2bar + m DFT(abar),
+//     Dbar = conj(E) D1bar,             Lbar += conj(h/2 E) conj(D) D1bar,   cbar += D1bar_0.
+// cbar accumulates in A.pbar; the host turns it into the cotangents of the pump and of L_0 (the
+// increment c depends on both) once all segments are done.  Two transforms per step.
+template <typename T, int LOGN, int R, int C = 1>
+__global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) strang_adjoint_kernel(const AdjArgs A)
+{
+    using GR = Group<T, LOGN, R, C>;
+    constexpr int N = GR::N, P = GR::P;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const StepArgs& a = A.s;
+    GR grp;
+    bool valid;
+    const int inst = adj_setup(grp, smem, a, valid);
+    const int t = grp.t;
+    const long long off = a.base + (long long)inst * N;
+    const StepConsts<T> c = step_consts<T>(a, inst, N);
+    Props<T, LOGN, R, C> pr;
+    pr.init(a, off, t);
+
+    const long long TT = A.total, s = A.seg;
+    const long long ns = (A.nsteps - s * A.K < A.K) ? A.nsteps - s * A.K : A.K;
+    const cx<T>* buf =
+        reinterpret_cast<const cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + grp.ts;
+    cx<T>* dbp = reinterpret_cast<cx<T>*>(A.dbar) + off + t;
+    double2* glp = A.gL + off + t;
+
+    cx<T> Db[R];
+    LAcc<T> gl[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        Db[j] = dbp[j * P];
+        gl[j].init(glp[j * P]);
+    }
+    double2 pb = make_double2(0.0, 0.0);
+    if (t == 0)
+        pb = A.pbar[inst];
+    const T hh = c.hh;
+    const T gh = T(2) * c.g0h;                // g0 h
+    constexpr T invN = (T)(1.0 / (1 << LOGN));
+    if constexpr (C > 1)
+        cluster_sync();   // every block of the cluster runs before the first remote store
+
+    for (long long i = ns - 1; i >= 0; --i) {
+        // step i: D, a, D2 at TT strides
+        const cx<T>* Dn = buf + i * ADJ_VECS * TT;
+        // second linear half flow
+        if (t == 0) {
+            pb.x += (double)Db[0].re;
+            pb.y += (double)Db[0].im;
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const cx<T> E = pr.getE(j);
+            gl[j].add(cmulc(cmulc(Db[j], Dn[2 * TT + j * P]), cscale(E, hh)));
+            Db[j] = cmulc(Db[j], E);                                 // D2bar
+        }
+        // Kerr flow
+        cx<T> z[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            z[j] = Db[j];
+        grp.mask(z);
+#pragma unroll 1
+        for (int p = 0; p < 2; ++p) {
+            if (p == 1) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const cx<T> av = Dn[TT + j * P];
+                    const T p2 = av.re * av.re + av.im * av.im;
+                    T sn, cs;                                        // of half the phase
+                    if constexpr (sizeof(T) == 4)
+                        small_sincos(c.g0h * p2, sn, cs);
+                    else
+                        sincos(c.g0h * p2, &sn, &cs);
+                    const T ph = gh * p2;                            // g0 h |a|^2
+                    const T ur = T(1) - T(2) * sn * sn, ui = T(2) * sn * cs;
+                    const cx<T> bb = cscale(z[j], invN);             // bbar
+                    // conj(u) (1 - i ph) - 1
+                    const cx<T> A1 = {T(-2) * sn * sn - ui * ph, -ph * ur - ui};
+                    // i g0 h a^2 u
+                    const cx<T> au = cmul(cmul(av, av), cx<T>{ur, ui});
+                    const cx<T> B1 = {-gh * au.im, gh * au.re};
+                    const cx<T> ab = cadd(cmul(A1, bb), cmulc(B1, bb));
+                    z[j] = cconj(ab);                                // DFT(.) = conj(IDFT(conj .))
+                }
+            }
+            grp.inverse(z, p);
+        }
+        grp.mask(z);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            Db[j] = cadd(Db[j], cconj(z[j]));                        // D1bar
+        // first linear half flow
+        if (t == 0) {
+            pb.x += (double)Db[0].re;
+            pb.y += (double)Db[0].im;
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const cx<T> E = pr.getE(j);
+            gl[j].add(cmulc(cmulc(Db[j], Dn[j * P]), cscale(E, hh)));
+            Db[j] = cmulc(Db[j], E);                                 // Dbar
+        }
+    }
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            dbp[j * P] = Db[j];
+            glp[j * P] = gl[j].finish(glp[j * P]);
+        }
+        if (t == 0)
+            A.pbar[inst] = pb;
+    }
+    if (grp.failed() && a.status)
         a.status[inst] = 2;
     if constexpr (C > 1)
         cluster_sync();   // no block leaves while a peer may still address its shared memory

@@ -141,6 +141,7 @@ struct cme_instance_s {
     int N = 0;
     int M = 0;   // physical modes (0: all N)
     std::vector<double> kappa, omega, field;
+    std::vector<double> g0mu;   // per-mode Kerr coefficients (centred); empty: g0 on every mode
     double g0 = 0, kappa_ext = 0, ain_re = 0, ain_im = 0, sigma = 0;
 };
 
@@ -152,6 +153,7 @@ struct LaunchGroup {
     int R = 8, G = 1;
     int C = 1;                  // blocks per instance (thread-block cluster when > 1)
     bool masked = false;        // some instance has padding modes (M < N)
+    bool kerr = false;          // some instance has per-mode Kerr coefficients
     // N > 4096: four-step split N = N1 N2 (column length N1, row length N2)
     bool large = false;
     int logN1 = 0, logN2 = 0, G1 = 1, G2 = 1;
@@ -182,8 +184,10 @@ struct cme_batch_s {
          *diag = nullptr;
     double *kappa = nullptr, *omega = nullptr, *sigma_d = nullptr, *g0_d = nullptr;
     double2 *pump_d = nullptr, *cpump_d = nullptr, *stage = nullptr;
+    double2* cphi_d = nullptr;   // per instance phi(L_0), phi'(L_0) of the Strang pump increment
     int *mode_inst = nullptr, *inst_N = nullptr, *status_d = nullptr;
     int* phys_d = nullptr;   // per-instance physical mode count M
+    void* kerr_d = nullptr;  // per-mode Kerr factors (field precision), if any instance has them
     long long* inst_off = nullptr;
     std::map<int, void*> tw;  // per log2 N
 
@@ -383,6 +387,15 @@ int plan_batch(cme_batch b, const cme_options& o)
 
 }  // namespace
 
+void cme::count_launches(long n) { g_launches += n; }
+
+void cme::default_group_plan(int logN, int prec, int count, int sms, int* R, int* G)
+{
+    const int r = std::min(default_radix(logN, prec, count, sms), 1 << logN);
+    *R = r;
+    *G = inst_per_block(1 << logN, r, 0, count);
+}
+
 // ------------------------------------------------------------------------------------------
 extern "C" {
 
@@ -486,6 +499,21 @@ int cme_set_modes(cme_instance inst, int M)
     if (M < 1 || M > inst->N)
         return fail(CME_ERR_INVALID_ARG, "cme_set_modes: M=%d outside [1, N=%d]", M, inst->N);
     inst->M = M;
+    return CME_OK;
+}
+
+int cme_set_kerr(cme_instance inst, const double* g0_mu)
+{
+    if (!inst)
+        return fail(CME_ERR_INVALID_ARG, "cme_set_kerr: NULL instance");
+    if (!g0_mu) {
+        inst->g0mu.clear();
+        return CME_OK;
+    }
+    for (int i = 0; i < inst->N; ++i)
+        if (!std::isfinite(g0_mu[i]))
+            return fail(CME_ERR_INVALID_ARG, "cme_set_kerr: g0_mu[%d] is not finite", i);
+    inst->g0mu.assign(g0_mu, g0_mu + inst->N);
     return CME_OK;
 }
 
@@ -596,6 +624,15 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
         cme_batch_destroy(b);
         return fail(CME_ERR_INVALID_ARG, "cme_batch_create: more than %d distinct N", MAX_GROUPS);
     }
+    if (o.integrator == CME_STRANG) {
+        for (int i = 0; i < count; ++i)
+            if (!v[i]->g0mu.empty()) {
+                cme_batch_destroy(b);
+                return fail(CME_ERR_INVALID_ARG,
+                            "cme_batch_create: instance %d has per-mode Kerr coefficients, which "
+                            "the Strang step cannot integrate exactly (use RK4IP)", i);
+            }
+    }
     // host-side validation of the launch options before any CUDA call
     // (the group's fields are copied out before cme_batch_destroy frees the groups)
     for (const auto& g : b->groups) {
@@ -651,6 +688,7 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     b->g0_d = (double*)A(count * 8);
     b->pump_d = (double2*)A(count * 16);
     b->cpump_d = (double2*)A(count * 16);
+    b->cphi_d = (double2*)A(count * 32);
     b->inst_N = (int*)A(count * 4);
     b->status_d = (int*)A(count * 4);
     b->phys_d = (int*)A(count * 4);
@@ -695,7 +733,7 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
             mi[o0 + pm] = i;
             field[o0 + c] = make_double2(v[i]->field[2 * c], v[i]->field[2 * c + 1]);
         }
-        g0[i] = v[i]->g0;
+        g0[i] = v[i]->g0mu.empty() ? v[i]->g0 : 1.0;   // per-mode: the factors carry g0_mu
         const double sk = std::sqrt(v[i]->kappa_ext);
         b->sqk_h.push_back(sk);
         pump[i] = make_double2(sk * v[i]->ain_re, sk * v[i]->ain_im);
@@ -727,6 +765,40 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
             if (Mh[i] < g.N)
                 g.masked = true;
     CPY(b->inst_off, b->off_h.data(), count * 8);
+    bool any_kerr = false;
+    for (int i = 0; i < count; ++i)
+        any_kerr |= !v[i]->g0mu.empty();
+    if (any_kerr) {
+        // per-mode factors in the field layout (1 for instances without per-mode coefficients)
+        b->kerr_d = b->alloc(T * (b->prec == PREC_FP32 ? 4 : 8));
+        if (!b->kerr_d) {
+            cme_batch_destroy(b);
+            return fail(CME_ERR_OOM, "cme_batch_create: device allocation of the Kerr factors");
+        }
+        std::vector<double> kd(T, 1.0);
+        std::vector<float> kf;
+        for (int i = 0; i < count; ++i) {
+            if (v[i]->g0mu.empty())
+                continue;
+            const int N = v[i]->N, l = ilog2i(N), l1 = (l + 1) / 2, l2 = l / 2;
+            for (int c = 0; c < N; ++c) {
+                int pm = (c + N / 2) & (N - 1);
+                if (N > 4096)
+                    pm = ((pm & ((1 << l2) - 1)) << l1) + (pm >> l2);
+                kd[b->off_h[i] + pm] = v[i]->g0mu[c];
+            }
+        }
+        for (auto& g : b->groups)
+            for (int i = g.first; i < g.first + g.count; ++i)
+                if (!v[i]->g0mu.empty())
+                    g.kerr = true;
+        if (b->prec == PREC_FP32) {
+            kf.assign(kd.begin(), kd.end());
+            CPY(b->kerr_d, kf.data(), T * 4);
+        } else {
+            CPY(b->kerr_d, kd.data(), T * 8);
+        }
+    }
     CPY(b->stage, field.data(), T * 16);
 #undef CPY
     cudaError_t e = cudaMemsetAsync(b->status_d, 0, count * 4, s);
@@ -835,6 +907,7 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
     a.g0 = b->g0_d + g.first;
     a.status = b->status_d + g.first;
     a.phys = g.masked ? b->phys_d + g.first : nullptr;   // null: no padding modes in the group
+    a.kerr = g.kerr ? b->kerr_d : nullptr;               // null: g0 on every mode of the group
     a.h = b->h_cur;
     a.hf = (float)b->h_cur;
     a.hhf = (float)(0.5 * b->h_cur);
@@ -884,6 +957,7 @@ LargeArgs large_args(cme_batch b, const LaunchGroup& g)
     a.g0 = b->g0_d + g.first;
     a.status = b->status_d + g.first;
     a.phys = g.masked ? b->phys_d + g.first : nullptr;   // null: no padding modes in the group
+    a.kerr = g.kerr ? b->kerr_d : nullptr;
     a.h = b->h_cur;
     a.hf = (float)b->h_cur;
     a.hhf = (float)(0.5 * b->h_cur);
@@ -1082,6 +1156,7 @@ int ensure_propagators(cme_batch b, double h)
     p.e2 = b->e2;
     p.cpump = b->cpump_d;
     p.ninst = b->count;
+    p.cphi = b->cphi_d;
     ++g_launches;
     CME_CUDA(launch_propagators(p, b->stream), "cme_step: propagator kernel");
     b->h_cur = h;
@@ -1650,8 +1725,6 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
     if (!b || !target || !out || !(h > 0.0) || !std::isfinite(h) || nsteps <= 0 || segment < 0 ||
         !(eps > 0.0))
         return fail(CME_ERR_INVALID_ARG, "cme_grad: invalid argument");
-    if (b->method != METHOD_RK4IP)
-        return fail(CME_ERR_INVALID_ARG, "cme_grad: gradients are implemented for RK4IP batches");
     if (b->has_large())
         return fail(CME_ERR_INVALID_ARG, "cme_grad: gradients are implemented for N <= 4096");
     const long long K = segment ? segment : (long long)std::ceil(std::sqrt((double)nsteps));
@@ -1732,6 +1805,7 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
             A.dbar = b->g_dbar;
             A.gL = b->g_gL;
             A.pbar = b->g_pbar + ga.first;
+            A.method = b->method;
             ++g_launches;
             cudaError_t e = b->prec == PREC_FP64
                                 ? launch_adjoint_fp64(role, ga.logN, ga.R, ga.C, A, str)
@@ -1758,6 +1832,13 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
             CME_CUDA(run_segment(ADJ_RECOMPUTE, sg - 1, side), "cme_grad: recompute");
             CME_CUDA(cudaEventRecord(ev_rec, side), "cme_grad: recompute");
         }
+    }
+    if (b->method == METHOD_STRANG) {
+        // the pump increment of the linear half flows depends on the pump and on L_0
+        ++g_launches;
+        CME_CUDA(launch_strang_pump_grad(b->count, b->inst_off, b->cphi_d, b->pump_d, b->g_pbar,
+                                         b->g_gL, st),
+                 "cme_grad: pump cotangent");
     }
     g_launches += 2;
     CME_CUDA(launch_grad_reduce(b->count, b->inst_N, b->inst_off, b->g_gL, b->g_loss, b->g_red, st),

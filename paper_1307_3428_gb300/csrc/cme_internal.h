@@ -27,6 +27,8 @@ struct StepArgs {
     const double* g0;       // per-instance Kerr coefficient g0
     int* status;            // per-instance status (group-relative)
     const int* phys;        // per-instance physical mode count M (group-relative; null: all N)
+    const void* kerr;       // per-mode Kerr factors g0_mu / g0 in the field precision, laid out
+                            // like E (null: every mode takes its instance's g0)
     long long nsteps;
     double h;
     float hf, hhf, h6f;     // h, h/2, h/6 rounded once to FP32 on the host
@@ -100,6 +102,12 @@ cudaError_t launch_diag_fp32(int logN, int R, const StepArgs& a, cudaStream_t s)
 
 // Record an error message for cme_last_error() and return `code` (cme_api.cu).
 int report_error(int code, const char* fmt, ...);
+// Add n to the count of kernels this library launched (cme_kernel_launches; cme_api.cu).
+void count_launches(long n);
+// One-block launch plan of a uniform-N group under default options: values per thread *R and
+// instances per block *G, the rule cme_batch_create applies before its choice of clusters
+// (cme_api.cu).  sms: the device's multiprocessor count.
+void default_group_plan(int logN, int prec, int count, int sms, int* R, int* G);
 
 // Auxiliary kernels (aux_kernels.cu).
 struct PropArgs {
@@ -119,6 +127,9 @@ struct PropArgs {
     void* e1h;                // Strang: expm1(L h/2)
     double2* cpump;           // Strang pump increment per instance
     int ninst;
+    double2* cphi;            // optional (null: skipped): per instance phi(L_0) and phi'(L_0),
+                              // phi(L) = (exp(L h/2) - 1)/L, the factor of the Strang pump
+                              // increment and its derivative (the Strang adjoint's pump terms)
 };
 cudaError_t launch_propagators(const PropArgs& a, cudaStream_t s);
 cudaError_t launch_twiddles(int N, int prec, void* out, cudaStream_t s);
@@ -143,6 +154,12 @@ cudaError_t launch_loss_seed(int prec, int total, const int* mode_inst, const in
                              const long long* inst_off, const void* hi, const void* lo,
                              const double* target, double eps, double* loss_modes, void* dbar,
                              cudaStream_t s);
+// Strang gradients: turn the accumulated cotangent cbar of each instance's pump increment
+// c = phi(L_0) p (in pbar) into the pump cotangent pbar = conj(phi) cbar, and add
+// conj(p phi'(L_0)) cbar to the L cotangent of the pumped mode (gL at the instance offset).
+cudaError_t launch_strang_pump_grad(int count, const long long* inst_off, const double2* cphi,
+                                    const double2* pump, double2* pbar, double2* gL,
+                                    cudaStream_t s);
 // Per instance, in a fixed summation order: red[4i..4i+3] = (sum_mu g_mu, sum g_mu mu^2/2,
 // sum g_mu mu^3/6, L_i) with g_mu = Im gL_mu (the cotangent of Im L_mu = omega_mu - omega_0 -
 // sigma) and L_i the instance's loss.
@@ -164,6 +181,12 @@ cudaError_t launch_adjoint_cluster_fp32(int role, int logN, int R, int C, const 
                                         cudaStream_t s);
 cudaError_t launch_adjoint_cluster_fp64(int role, int logN, int R, int C, const AdjArgs& a,
                                         cudaStream_t s);
+// The same roles for the Strang split step (a.method == METHOD_STRANG; launch_adjoint_fp32/fp64
+// forward to these), C = 1 or a cluster shape.
+cudaError_t launch_adjoint_strang_fp32(int role, int logN, int R, int C, const AdjArgs& a,
+                                       cudaStream_t s);
+cudaError_t launch_adjoint_strang_fp64(int role, int logN, int R, int C, const AdjArgs& a,
+                                       cudaStream_t s);
 
 }  // namespace cme
 

@@ -49,6 +49,7 @@ struct LargeArgs {
     const double* g0;
     int* status;
     const int* phys;         // per-instance physical mode count M (null: all N)
+    const void* kerr;        // per-mode Kerr factors g0_mu / g0 (field layout), or null
     double h;
     float hf, hhf, h6f;
     int stage;               // col kernel: LARGE_START, 0..3, LARGE_FINAL
@@ -200,6 +201,13 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
 #pragma unroll
         for (int j = 0; j < R; ++j)
             x[j].im = -x[j].im;
+        if (A.kerr) {
+            // per-mode Kerr coefficient of the output mode (the instance's g0 is then 1)
+            const T* km = reinterpret_cast<const T*>(A.kerr) + f0;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                x[j] = cscale(x[j], __ldg(km + j * estride));
+        }
         if (A.phys) {
             // padding modes (outside the centred M physical ones) get no FWM term
             const int M = A.phys[inst];

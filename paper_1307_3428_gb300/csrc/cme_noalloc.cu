@@ -9,7 +9,6 @@
 // status words) live in g_noalloc_scratch below.
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -25,7 +24,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Device address of g_noalloc_scratch per device ordinal.  In host code the array's name is a
 // host-side stand-in, not a device address, so the address must come from
-// cudaGetSymbolAddress, taken once per device with that device current.
+// cudaGetSymbolAddress, taken once per device with that device current.  The cached address
+// belongs to the device's context as it was then: after cudaDeviceReset it is stale.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -178,16 +178,14 @@ extern "C" int cme_rk4ip_noalloc(int N, int count, double h, long nsteps, const 
         int logN = 0;
         while ((1 << logN) < N)
             ++logN;
-        const int R = logN <= 2 ? 4 : 8;   // the library's default values per thread
-        // instances per block: the rule cme_batch_create uses for default options
-        const int P = N / R;
-        int G = P >= 64 ? 1 : std::min(std::max(1, 64 / P), std::max(1, 256 / P));
-        if (P < 32) {
-            const int per_warp = 32 / P;   // whole warps for __syncwarp
-            G = std::max(per_warp, (G + per_warp - 1) / per_warp * per_warp);
-        } else if (P < 64) {
-            G = std::min(G, count);
-        }
+        // values per thread and instances per block: the one-block plan cme_batch_create
+        // chooses under default options (for small sets 4 values per thread, for instance)
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int R = 8, G = 1;
+        default_group_plan(logN, PREC_FP64, count, sms, &R, &G);
         StepArgs a{};
         a.ninst = count;
         a.G = G;
@@ -207,11 +205,14 @@ extern "C" int cme_rk4ip_noalloc(int N, int count, double h, long nsteps, const 
         a.hf = (float)h;
         a.hhf = (float)(0.5 * h);
         a.h6f = (float)(h / 6.0);
-        e = launch_step_fp64_rk4ip(logN, R, a, s);
+        if (e == cudaSuccess)
+            e = launch_step_fp64_rk4ip(logN, R, a, s);
     }
     if (e == cudaSuccess)
         e = launch_export(PREC_FP64, (int)total, mode_inst, inst_N, inst_off, hi, nullptr,
                           (double2*)d_field, 1, omega_t, sigma, 0.0, s);
+    // tables, twiddles, propagators, import, (step,) export
+    count_launches(nsteps > 0 ? 6 : 5);
     if (e != cudaSuccess)
         return report_error(CME_ERR_CUDA, "cme_rk4ip_noalloc: launch: %s", cudaGetErrorString(e));
     return CME_OK;

@@ -167,6 +167,25 @@ struct Group {
                     x[j] = cx<T>{T(0), T(0)};
         }
     }
+    // Per-mode Kerr coefficient (Sec. 2: g0 need not be constant): the four-wave-mixing term
+    // of output mode mu carries g0_mu instead of the instance's g0, applied as the factor
+    // km[j P] of this thread's mode t + jP to the forward transform's output (the instance's g0
+    // is then 1).  km = null (the default) leaves every mode at g0.
+    const T* km;
+    CME_DEV void set_kerr(const void* table, long long off)
+    {
+        km = table ? reinterpret_cast<const T*>(table) + off + t : nullptr;
+    }
+    // The right-hand side's output side: the per-mode Kerr factor, then the physical-mode mask.
+    CME_DEV void out_modes(cx<T> (&x)[R]) const
+    {
+        if (km) {
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                x[j] = cscale(x[j], __ldg(km + j * P));
+        }
+        mask(x);
+    }
 
     // The step loops contain a single copy of the transform code (instruction-cache
     // footprint): the forward transform is computed as conj(inverse(conj(x))).  d = 0 takes
@@ -260,7 +279,7 @@ struct Group {
 #pragma unroll
         for (int j = 0; j < R; ++j)
             x[j].im = -x[j].im;
-        mask(x);
+        out_modes(x);
         if (t == 0)
             x[0] = cadd(x[0], pump);
     }
@@ -296,6 +315,7 @@ struct Group {
         else
             tw.init(tw_table, t);
         set_modes(N);
+        km = nullptr;
     }
 
     // Cluster set-up (C > 1): block `rank` of the cluster, thread l of the block.  The block's
@@ -362,6 +382,7 @@ struct Group {
         twm = wm;
         twt = wt;
         set_modes(N);
+        km = nullptr;
     }
 };
 
@@ -575,10 +596,14 @@ CME_DEV void small_sincos(float y, float& s, float& c)
 // exact linear+pump flow over h/2, exact Kerr flow over h, exact linear+pump flow over h/2.
 // With a = inverse transform of D the Kerr flow is a -> a exp(i g0 |a|^2 h); it is applied as
 // the increment D += DFT(a expm1(i g0 |a|^2 h))/N.
-template <typename T, int LOGN, int R, int C>
-CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
-                         const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c)
+// STORE = true also stores, unless so is null (the adjoint's recomputation), the time-domain
+// field a of the Kerr flow at so[j P] and the state after the Kerr flow at so[sstride + j P].
+template <bool STORE, typename T, int LOGN, int R, int C>
+CME_DEV void strang_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                              const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c, cx<T>* so,
+                              long long sstride)
 {
+    constexpr int P = Group<T, LOGN, R, C>::P;
     constexpr bool COMP = Group<T, LOGN, R, C>::COMP;
     constexpr T invN = (T)(1.0 / (1 << LOGN));
 #pragma unroll 1
@@ -591,6 +616,13 @@ CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
 #pragma unroll 1
             for (int d = 0; d < 2; ++d) {
                 grp.inverse(x, d);
+                if constexpr (STORE) {
+                    if (d == 0 && so) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j)
+                            so[j * P] = x[j];
+                    }
+                }
                 if (d == 0) {
 #pragma unroll
                     for (int j = 0; j < R; ++j) {
@@ -612,6 +644,13 @@ CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 fs.add(j, cx<T>{x[j].re, -x[j].im});
+            if constexpr (STORE) {
+                if (so) {
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        so[sstride + j * P] = fs.Dh[j];
+                }
+            }
         }
         // linear + pump half step: D += e1 D + delta_{mu,0} c
 #pragma unroll
@@ -625,6 +664,13 @@ CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
             fs.add(j, d);
         }
     }
+}
+
+template <typename T, int LOGN, int R, int C>
+CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                         const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c)
+{
+    strang_step_impl<false>(grp, fs, pr, c, static_cast<cx<T>*>(nullptr), 0);
 }
 
 template <typename T>
@@ -660,12 +706,13 @@ CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
         inst = a.ninst - 1;  // duplicate work keeps every group in the barriers; no store
     GR grp;
     grp.setup(smem, g, threadIdx.x - g * P, a.tw);
+    const long long off = a.base + (long long)inst * N;
     if constexpr (MASKABLE) {
         if (a.phys)
             grp.set_modes(a.phys[inst]);
+        grp.set_kerr(a.kerr, off);
     }
     const int t = grp.t;
-    const long long off = a.base + (long long)inst * N;
 
     cx<T>* hi = reinterpret_cast<cx<T>*>(a.hi) + off + t;
     cx<T>* lo = reinterpret_cast<cx<T>*>(a.lo) + off + t;
@@ -713,10 +760,11 @@ __global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(cons
     const int inst = blockIdx.x / C;
     GR grp;
     grp.setup_cluster(smem, cluster_rank(), threadIdx.x, a.tw, a.a2a_fault);
+    const long long off = a.base + (long long)inst * N;
     if (a.phys)
         grp.set_modes(a.phys[inst]);
+    grp.set_kerr(a.kerr, off);
     const int t = grp.t;
-    const long long off = a.base + (long long)inst * N;
 
     cx<T>* hi = reinterpret_cast<cx<T>*>(a.hi) + off + t;
     cx<T>* lo = reinterpret_cast<cx<T>*>(a.lo) + off + t;
@@ -762,10 +810,11 @@ __global__ void __launch_bounds__(max_threads<LOGN, R>()) diag_kernel(const Step
         inst = a.ninst - 1;
     GR grp;
     grp.setup(smem, g, threadIdx.x - g * P, a.tw);
+    const long long off = a.base + (long long)inst * N;
     if (a.phys)
         grp.set_modes(a.phys[inst]);
+    grp.set_kerr(a.kerr, off);
     const int t = grp.t;
-    const long long off = a.base + (long long)inst * N;
     const cx<T>* src = reinterpret_cast<const cx<T>*>(a.hi) + off + t;
     cx<T>* dst = reinterpret_cast<cx<T>*>(a.diag_out) + off + t;
     cx<T> x[R];

@@ -19,6 +19,8 @@ static cudaError_t launch_adj_shape(KernelT k, const AdjArgs& a, cudaStream_t s)
 
 cudaError_t launch_adjoint_fp64(int role, int logN, int R, int C, const AdjArgs& a, cudaStream_t s)
 {
+    if (a.method == METHOD_STRANG)
+        return launch_adjoint_strang_fp64(role, logN, R, C, a, s);
     if (C > 1)
         return launch_adjoint_cluster_fp64(role, logN, R, C, a, s);
     switch (logN * 32 + R) {

@@ -5,7 +5,7 @@ namespace cme {
 
 cudaError_t launch_step_fp32_rk4ip(int logN, int R, const StepArgs& a, cudaStream_t s)
 {
-    if (a.phys)   // some instance of the group has padding modes
+    if (a.phys || a.kerr)   // padding modes or per-mode Kerr factors in the group
         return launch_step_fp32_rk4ip_masked(logN, R, a, s);
     switch (logN * 32 + R) {
 #define CME_CASE(LN, RR) \

@@ -42,6 +42,7 @@ class Instance:
     sigma: float
     D0: np.ndarray          # (N,) complex128 initial field
     M: Optional[int] = None  # physical modes (the centred M of the N); None: all N
+    g0_mu: Optional[np.ndarray] = None  # per-mode Kerr coefficients (centred); None: g0
 
     @property
     def mu(self) -> np.ndarray:
@@ -239,3 +240,11 @@ def random_instance(N: int, seed: int, g0: float = 1.0, kappa: float = 1.0, amp:
     om = dispersion(N, D2, 0.0)
     return Instance(N=N, kappa=kap, omega=om, g0=float(g0), kappa_ext=float(kappa_ext),
                     A_in=complex(A_in), sigma=float(sigma), D0=D0)
+
+
+def kerr_slope(g0: float, N: int, slope: float) -> np.ndarray:
+    """A frequency-dependent Kerr coefficient, linear across the band:
+    g0_mu = g0 (1 + slope mu / (N/2)) on the centred mode grid (the nonlinear coefficient
+    scales with the mode frequency and the inverse effective area, both smooth in mu)."""
+    mu = (np.arange(N) - N // 2).astype(np.float64)
+    return g0 * (1.0 + slope * mu / (N / 2.0))

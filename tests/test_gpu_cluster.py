@@ -86,7 +86,9 @@ def test_cluster_agrees_with_one_block(N, C, prec, integ):
         b.synchronize()
         out[c] = b.get_state()
         b.close()
-    assert rel(out[C], out[1]) <= (1e-12 if prec == cme.FP64 else 1e-5)
+    # measured (GB300): FP64 <= 7.5e-16; FP32 2.1e-7 ... 4.3e-7 (each side 0.9e-7 ... 2.1e-6
+    # from FP64, the cluster kernel within 1% of the one-block kernel's own error)
+    assert rel(out[C], out[1]) <= (1e-12 if prec == cme.FP64 else 1e-6)
 
 
 def test_cluster_inside_a_mixed_batch():
@@ -132,7 +134,10 @@ def test_cluster_adjoint_agrees_with_one_block(N, C, prec):
     """Against the one-block FP64 gradient.  In FP64 the cluster gradient agrees with it to
     rounding.  Parameter gradients are sums over modes that cancel, which FP32 determines only
     loosely, so the cluster FP32 gradient must be about as close to FP64 as the one-block FP32
-    gradient is: within 4 times its error (the two round in different orders), or 1e-5."""
+    gradient is: within 4 times its error, or 1e-6.  The two round in different orders, so
+    their errors are two draws of the same size: measured on GB300 over the 8 outputs of this
+    test and of test_cluster_adjoint_segment_lengths, the ratio of the cluster's error to the
+    one-block error lies between 0.75 and 2.51."""
     insts = [wl.make_instance(N, 0.01, 1e-4, 2.0 + k, 2.0, 1e-3, seed=3600 + k) for k in range(2)]
     T = np.concatenate([target_for(N, 3610 + k) for k in range(2)])
 
@@ -151,7 +156,7 @@ def test_cluster_adjoint_agrees_with_one_block(N, C, prec):
         one = grad(prec, 1)
         for key in ref:
             e1, eC = rel(one[key], ref[key]), rel(got[key], ref[key])
-            assert eC <= max(4 * e1, 1e-5), (key, e1, eC)
+            assert eC <= max(4 * e1, 1e-6), (key, e1, eC)
 
 
 @pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
@@ -211,7 +216,8 @@ def test_cluster_adjoint_segment_lengths(segment):
     """The FP32 backward kernel on clusters prefetches the next step's stored data into shared
     memory (two buffers, bulk copies).  Segments of 1, 2 and 7 steps cover the single-step
     segment and both buffer parities; each gradient must be as close to the one-block FP64
-    gradient as the one-block FP32 gradient is (within 4 times its error, or 1e-5)."""
+    gradient as the one-block FP32 gradient is (within 4 times its error, or 1e-6; see
+    test_cluster_adjoint_agrees_with_one_block for the measured spread)."""
     N = 4096
     insts = [wl.make_instance(N, 0.01, 1e-4, 2.0 + k, 2.0, 1e-3, seed=3900 + k) for k in range(2)]
     T = np.concatenate([target_for(N, 3910 + k) for k in range(2)])
@@ -227,4 +233,4 @@ def test_cluster_adjoint_segment_lengths(segment):
     got = grad(cme.FP32, 4, segment)
     for key in ref:
         e1, eC = rel(one[key], ref[key]), rel(got[key], ref[key])
-        assert eC <= max(4 * e1, 1e-5), (key, e1, eC)
+        assert eC <= max(4 * e1, 1e-6), (key, e1, eC)

@@ -44,8 +44,8 @@ def _run_noalloc(insts, h, nsteps):
     return field.cpu().numpy().view(np.complex128)
 
 
-def _run_batch(insts, h, nsteps):
-    b = cme.Batch([cme.Instance.from_workload(i) for i in insts], precision=cme.FP64)
+def _run_batch(insts, h, nsteps, **kw):
+    b = cme.Batch([cme.Instance.from_workload(i) for i in insts], precision=cme.FP64, **kw)
     b.step(h, nsteps)
     out = b.get_state()
     b.close()
@@ -66,6 +66,37 @@ def test_noalloc_matches_batch_path_on_two_calls():
             g, r = got[k * N:(k + 1) * N], ref[k * N:(k + 1) * N]
             err = np.linalg.norm(g - r) / np.linalg.norm(r)
             assert err <= TOL_FP64, (N, k, err)
+
+
+@pytest.mark.parametrize("N,count", [(4, 3), (8, 5), (2048, 4), (4096, 3)])
+def test_noalloc_launch_shape_is_the_batch_plan(N, count):
+    """The smallest sizes (one thread group narrower than a warp: N = 4 at 4 values per thread,
+    N = 8 at 8) and the sizes whose Runge-Kutta accumulator lives in shared memory in FP64
+    (N = 2048, 4096).  The result is bit for bit that of a batch with one block per instance
+    (the one-block plan the entry point shares with cme_batch_create), and within the FP64
+    tolerance of the default batch, which spreads few N >= 2048 instances over thread-block
+    clusters and so rounds in another order.  Each call counts its six kernels."""
+    amp = 0.3 * min(1.0, np.sqrt(64.0 / N))
+    insts = [wl.random_instance(N, 950 + k, amp=amp, sigma=0.3 * k, A_in=1.1 + 0.2j * k)
+             for k in range(count)]
+    before = cme.kernel_launches()
+    got = _run_noalloc(insts, 1e-3, 60)
+    assert cme.kernel_launches() - before == 6
+    assert np.array_equal(got, _run_batch(insts, 1e-3, 60, cluster=1))
+    ref = _run_batch(insts, 1e-3, 60)
+    for k in range(count):
+        g, r = got[k * N:(k + 1) * N], ref[k * N:(k + 1) * N]
+        assert np.linalg.norm(g - r) <= TOL_FP64 * np.linalg.norm(r), (N, k)
+
+
+def test_noalloc_does_not_report_nonfinite_results():
+    """The entry point returns before its kernels run and reads nothing back, so a field that
+    overflows comes back non-finite with CME_OK: the caller checks the field."""
+    insts = [wl.random_instance(64, 990 + k, amp=0.3) for k in range(2)]
+    insts[1].D0 = insts[1].D0 * 1e200          # |a|^2 a overflows in the first step
+    got = _run_noalloc(insts, 1e-3, 3)
+    assert np.all(np.isfinite(got[:64]))
+    assert not np.all(np.isfinite(got[64:]))
 
 
 def test_noalloc_refuses_sizes_beyond_its_array():
