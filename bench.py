@@ -318,9 +318,9 @@ def run_adjoint(args, world, rank, local):
     launches0 = cme.kernel_launches()
     t32, g32, clocks = timed(cme.FP32, nsteps, args.steps, args.warmup, ClockSampler(local))
     launches = (cme.kernel_launches() - launches0) // (args.steps + args.warmup)
-    n64 = min(nsteps, 1000)
-    t64, g64, _ = timed(cme.FP64, n64, 1, 1)
-    _, g32s, _ = timed(cme.FP32, n64, 1, 1)
+    # the FP64 gradient of the same workload, full horizon: the supported gradient of this
+    # configuration and the reference of the FP32 gradient's error
+    t64, g64, _ = timed(cme.FP64, nsteps, 1, 1)
     mode_steps = N * B * nsteps
     # forward, recomputation and backward: three times the forward step's 8 transforms of
     # 5 N log2 N flop plus ~80 pointwise flop per mode
@@ -344,15 +344,83 @@ def run_adjoint(args, world, rank, local):
                      "frac": achieved / peak, "traffic": None,
                      "basis": "3 x (8 transforms of 5 N log2 N + 80) flop per mode-step: forward, "
                               "checkpoint recomputation, backward"},
-        "fp64": {"value": N * B * n64 / t64, "steps": n64},
-        "error": {"fp32_vs_fp64_at_%d_steps" % n64: {
-            "loss": rel(g32s["loss"], g64["loss"]), "d_sigma": rel(g32s["d_sigma"], g64["d_sigma"]),
-            "d_A_in": rel(g32s["d_A_in"], g64["d_A_in"]), "d_D0": rel(g32s["d_D0"], g64["d_D0"])}},
+        "fp64": {"value": N * B * nsteps / t64, "steps": nsteps, "ms": t64 * 1e3,
+                 "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
+                              "achieved": flops / t64 / 1e12,
+                              "frac": flops / t64 / 1e12 / FP64_NOMINAL_TFLOPS},
+                 "note": "the FP64 gradient is the supported one at this configuration: the FP32 "
+                         "gradients of dL/dD2 and dL/dD3 are dominated by noise-floor modes that "
+                         "FP32 transforms do not resolve (error.full_horizon)"},
+        "error": {"full_horizon": {
+            "steps": nsteps,
+            "what": "FP32 gradient against the FP64 gradient of the same run: max over the "
+                    "batch of |difference| / max |FP64 value|",
+            "loss": rel(g32["loss"], g64["loss"]), "d_sigma": rel(g32["d_sigma"], g64["d_sigma"]),
+            "d_A_in": rel(g32["d_A_in"], g64["d_A_in"]), "d_D2": rel(g32["d_D2"], g64["d_D2"]),
+            "d_D3": rel(g32["d_D3"], g64["d_D3"]), "d_D0": rel(g32["d_D0"], g64["d_D0"])}},
         "gpu_launches": int(launches),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------------------ large N
+# Algorithmic bytes per mode-step of the four-step RK4IP path (FP32, 8 B per complex value):
+# per RK stage the row kernel reads Y and writes Z (16 B); the column kernel reads Z and the
+# field, and the accumulator S, the propagators E, e1 or e2 as its stage needs them, and writes
+# S and Y (stages 0..2: 48, 56, 56 B); the last stage reads Z, D, S, the compensation word and
+# e2 and writes D, the compensation word and Y of the next step (64 B).  Constant twiddle-table
+# reads are not counted.
+LARGE_BYTES_PER_MODE_STEP = 4 * 16 + 48 + 56 + 56 + 64
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def large_n_roofline(args, sizes, nsteps, kern_ms, cme, alu):
+    """HBM and L2 roofline of the large-N (four-step) run: algorithmic bytes per step over the
+    device time of a step, against the measured HBM copy bandwidth and the library's L2-resident
+    copy bandwidth (cme_l2_peak on 2 x 16 MiB, measured here)."""
+    byts = sum(sizes) * LARGE_BYTES_PER_MODE_STEP * nsteps
+    achieved = byts / (kern_ms * 1e-3) / 1e9
+    peaks, kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    l2 = cme.l2_peak(32 << 20) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as fh:
+            ent = json.load(fh).get("large_n_fp32_octave")
+        if ent and ent.get("source_hash") == large_source_hash() and not args.radix:
+            traffic = ent.get("dram_bytes_per_step")
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic,
+            "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 8 "
+                             "kernels of one step (per step, not per launch)",
+            "peak_basis": f"MEASURED_PEAKS.json hbm_gbs ({kind})",
+            "bytes_per_mode_step": LARGE_BYTES_PER_MODE_STEP,
+            "l2": {"achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                   "peak_basis": "cme_l2_peak: copies between two L2-resident 16 MiB buffers, "
+                                 "this run"},
+            "alu": {k: alu[k] for k in ("achieved", "peak", "unit", "frac")},
+            "kernel": "large_row_kernel + large_col_kernel (8 per RK4IP step)"}
+
+
+LARGE_SOURCES = ["cme_core.cuh", "cme_step.cuh", "cme_large.cuh", "kern_large_fp32.cu"]
+
+
+def large_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in LARGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1307_3428_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------------------ GPU arm
@@ -365,9 +433,15 @@ def run_gpu(args, world, rank, local):
     from paper_1307_3428_gb300 import cme
     from paper_1307_3428_gb300 import workloads as wl
 
+    from paper_1307_3428_gb300 import shard
+
     torch.cuda.set_device(local)
     if args.workload == "sweep512":
-        w = wl.sweep512(seed_offset=256 * rank) if rank else wl.sweep512()
+        # weak scaling: the global batch is `world` replicas of the sweep with independent
+        # noise; each rank integrates its own shard (256 instances) of it
+        w = wl.sweep512()
+        global_insts = [i for r in range(world)
+                        for i in (wl.sweep512(seed_offset=256 * r) if r else w).instances]
     elif args.workload == "uneven":
         w = wl.uneven()
     elif args.workload == "plain64":
@@ -382,18 +456,25 @@ def run_gpu(args, world, rank, local):
         raise SystemExit(f"unknown workload {args.workload}")
     strang = args.strang or args.workload == "fig1"   # Fig. 1 is a split-step run
     headline = args.workload == "sweep512"
+    if not headline:
+        global_insts = list(w.instances) * world   # replicas of the whole workload per rank
     sizes = [i.N for i in w.instances]
     N = max(sizes)
     count = len(w.instances)
     nsteps = args.inner_steps or w.nsteps
     mode_steps = sum(sizes) * nsteps
 
-    insts = [cme.Instance.from_workload(i) for i in w.instances]
     prec_main = cme.FP64 if args.workload == "plain64" else cme.FP32
-    b32 = cme.Batch(insts, precision=prec_main, use_graph=True, radix=args.radix,
-                    inst_per_cta=args.inst_per_cta, persistent=args.persistent,
-                    cluster=args.cluster,
-                    integrator=cme.STRANG if strang else cme.RK4IP)
+    # this rank's shard of the global batch (instances are independent: no exchange while
+    # stepping; results cross ranks only through the host gather below)
+    sb = shard.ShardedBatch(global_insts, world=world, rank=rank, precision=prec_main,
+                            use_graph=True, radix=args.radix, inst_per_cta=args.inst_per_cta,
+                            persistent=args.persistent, cluster=args.cluster,
+                            integrator=cme.STRANG if strang else cme.RK4IP)
+    assert len(sb.local) == count, "one workload's worth of instances per rank"
+    w.instances = list(sb.local)
+    insts = [cme.Instance.from_workload(i) for i in w.instances]
+    b32 = sb.batch
     plan = None
     if args.autotune:
         plan = b32.autotune(w.h, probe_steps=200)
@@ -453,6 +534,12 @@ def run_gpu(args, world, rank, local):
         retimed = True
     step_ms = max_over_ranks(total_ms / args.steps, world)
     value = world * mode_steps / (step_ms * 1e-3)
+    # the global batch's final spectra gathered on rank 0, in global instance order
+    gathered = sb.spectrum(cme.POWER)
+    gather = None
+    if rank == 0:
+        gather = {"instances": len(global_insts), "modes": int(gathered.size),
+                  "all_finite": bool(np.all(np.isfinite(gathered)))}
 
     # roofline of the step kernel (one graph node per replay)
     kern_ms = statistics.mean(k_ms)
@@ -482,6 +569,10 @@ def run_gpu(args, world, rank, local):
                            else f"{args.workload} step kernel(s)"),
                 "peak_basis": ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"
                                if prec_main == cme.FP32 else "GB300 nominal FP64 1.25 TFLOP/s")}
+    if max(sizes) > 4096 and not strang:
+        # The four-step large-N path moves its state, propagators and inter-pass buffers
+        # through L2 every step: it is bound by memory, not by the FP32 ALUs.
+        roofline = large_n_roofline(args, sizes, nsteps, kern_ms, cme, roofline)
 
     # FP32 result vs FP64 over the whole batch, full horizon
     fin32 = b32.get_state()
@@ -520,9 +611,18 @@ def run_gpu(args, world, rank, local):
             e1.record(sp)
             e1.synchronize()
             tp.append(e0.elapsed_time(e1))
+        f_plain = 64 * p.nsteps * flops_per_mode_step(64) / (min(tp) * 1e-3) / 1e12
+        f_batch = flops / (ms64 * 1e-3) / 1e12
         fp64 = {
             "batched_value": mode_steps / (ms64 * 1e-3), "batched_ms": ms64,
+            "batched_roofline": {"bound": "alu", "achieved": f_batch, "unit": "TFLOP/s",
+                                 "peak": FP64_NOMINAL_TFLOPS, "frac": f_batch / FP64_NOMINAL_TFLOPS},
             "plain_n64_value": 64 * p.nsteps / (min(tp) * 1e-3), "plain_n64_ms": min(tp),
+            "plain_n64_roofline": {
+                "bound": "alu", "achieved": f_plain, "unit": "TFLOP/s",
+                "peak": FP64_NOMINAL_TFLOPS, "frac": f_plain / FP64_NOMINAL_TFLOPS,
+                "basis": "64 modes x 2000 steps x (40 log2 64 + 80) flop; one instance of 16 "
+                         "threads: latency of one thread's FP64 chain, not the FP64 pipes"},
             "unit": UNIT,
             "fp32_speedup_vs_batched_fp64": ms64 / kern_ms,
             "fp32_speedup_vs_plain_fp64": value / world / (64 * p.nsteps / (min(tp) * 1e-3)),
@@ -569,6 +669,7 @@ def run_gpu(args, world, rank, local):
         "fp64": fp64,
         "error": error,
         "wall_s_timed": wall,
+        "gather": gather,
     }
     if retimed:
         line["retimed_after_low_fma_rate"] = True

@@ -182,8 +182,10 @@ int cme_batch_plan(cme_batch b, int group, int* N, int* radix, int* inst_per_cta
 int cme_step(cme_batch b, double h, long nsteps);
 
 /* Pick the fastest launch plan for this batch and step size h by timing `probe_steps` steps of
- * each candidate (values per thread, instances per block, per-group vs persistent launch) on
- * the device; the field is saved before and restored after, so the batch state is unchanged.
+ * each candidate (values per thread, instances per block, blocks per instance, per-group vs
+ * persistent launch) on the device, each as one launch; then the best of them with the probe
+ * split into 4 and into 16 launches (steps_per_launch = probe_steps / 4, / 16), kept only where
+ * that is faster.  The field is saved before and restored after, so the batch state is unchanged.
  * The chosen plan replaces the batch's options for later cme_step calls; *plan_out (may be
  * NULL) receives it.  Synchronises.  Errors: INVALID_ARG, CUDA. */
 int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out);
@@ -325,6 +327,14 @@ int cme_set_allocator(cme_alloc_fn alloc, cme_free_fn release, void* ctx);
 /* Measured throughput of dependent-free fused multiply-adds on the current device, in
  * flop/s (2 flop per FMA), for CME_FP32 or CME_FP64; runs for a few tens of ms. */
 int cme_fma_peak(int precision, double* flops_per_s);
+
+/* Measured bandwidth of copying between two buffers of together at most `bytes` (1 MiB .. 1 GiB;
+ * each buffer the largest power of two of float4 that fits): read plus written bytes per
+ * second, best of four launches of 32 passes after a first launch that brings both buffers
+ * into the cache.  With `bytes` well under the 129 MB L2 of this GPU this is the L2 bandwidth
+ * a kernel whose working set stays in L2 can reach (the large-N kernels' roof); with more, the
+ * HBM bandwidth.  Allocates and frees its buffers; runs for a few ms. */
+int cme_l2_peak(size_t bytes, double* bytes_per_s);
 
 /* Number of kernels this library has launched in the calling process (for accounting). */
 long cme_kernel_launches(void);

@@ -698,7 +698,7 @@ int oracle_strang_grad(int N, int M, const double* kappa, const double* omega, d
         const double P = creal(Df[i]) * creal(Df[i]) + cimag(Df[i]) * cimag(Df[i]);
         const double r = log10(P + eps) - target[i];
         L += r * r;
-        const double dLdP = 2.0 * r / ((P + eps) * log(10.0));
+        const double dLdP = 2.0 * r / (log(10.0) * (P + eps));
         Db[i] = 2.0 * dLdP * Df[i];
     }
     *loss = L;

@@ -97,6 +97,7 @@ _SIGS = [
     ("cme_eval_rhs", ctypes.c_int, [_VP, _DP, ctypes.c_int]),
     ("cme_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, _VP]),
     ("cme_fma_peak", ctypes.c_int, [ctypes.c_int, _DP]),
+    ("cme_l2_peak", ctypes.c_int, [ctypes.c_size_t, _DP]),
     ("cme_kernel_launches", ctypes.c_long, []),
     ("cme_last_error", ctypes.c_char_p, []),
     ("cme_version", ctypes.c_char_p, []),
@@ -380,6 +381,13 @@ def rk4ip_noalloc(N: int, count: int, h: float, nsteps: int, d_kappa: int, d_ome
 def fma_peak(precision=FP32) -> float:
     v = ctypes.c_double()
     _check(load().cme_fma_peak(int(precision), ctypes.byref(v)))
+    return v.value
+
+
+def l2_peak(nbytes: int = 16 << 20) -> float:
+    """cme_l2_peak: copy bandwidth (read + write bytes/s) of an L2-resident buffer."""
+    v = ctypes.c_double()
+    _check(load().cme_l2_peak(int(nbytes), ctypes.byref(v)))
     return v.value
 
 

@@ -426,6 +426,71 @@ cudaError_t launch_grad_export(int prec, int total, const int* mode_inst, const 
     return cudaGetLastError();
 }
 
+// Copies within a buffer pair that stays resident in L2, `reps` passes per launch (float4 per
+// thread, grid-stride; pass r reads at a rotated offset, and the accesses are volatile PTX, so
+// no pass is merged with another).  For the L2 bandwidth the large-N kernels are measured
+// against.
+__device__ __forceinline__ float4 ld_v4(const float4* p)
+{
+    float4 v;
+    asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_v4(float4* p, float4 v)
+{
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w) : "memory");
+}
+__global__ void l2_copy_kernel(const float4* src, float4* dst, long long n, int reps)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            st_v4(dst + i, ld_v4(src + ((i + 4099LL * r) & (n - 1))));
+}
+
+cudaError_t run_l2_peak(size_t bytes, double* bytes_per_s)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    size_t n = 1;   // float4 elements per buffer: the largest power of two that fits
+    while (n * 2 * 16 <= bytes)
+        n *= 2;
+    void* buf = nullptr;
+    e = cudaMalloc(&buf, 2 * n * 16);
+    if (e != cudaSuccess)
+        return e;
+    cudaMemset(buf, 0, 2 * n * 16);
+    const float4* src = reinterpret_cast<const float4*>(buf);
+    float4* dst = reinterpret_cast<float4*>(buf) + n;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    const int reps = 32;
+    for (int rep = 0; rep < 5; ++rep) {
+        cudaEventRecord(a);
+        l2_copy_kernel<<<sms * 4, 512>>>(src, dst, (long long)n, reps);
+        cudaEventRecord(b);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best)   // the first launch brings the buffers into L2
+            best = ms;
+    }
+    e = cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(buf);
+    *bytes_per_s = 2.0 * (double)n * 16.0 * reps / (best * 1e-3);
+    return e;
+}
+
 cudaError_t run_fma_peak(int prec, double* flops)
 {
     int dev = 0, sms = 0;

@@ -146,6 +146,7 @@ cudaError_t launch_export_plain(int prec, int total, const int* mode_inst, const
                                 const long long* inst_off, const void* src, double2* dst,
                                 int reorder_centred, cudaStream_t s);
 cudaError_t run_fma_peak(int prec, double* flops);
+cudaError_t run_l2_peak(size_t bytes, double* bytes_per_s);
 
 // Gradient helpers (aux_kernels.cu).
 // Log-power-spectrum misfit terms (log10(|D_mu|^2 + eps) - T_mu)^2 per mode (loss_modes) and

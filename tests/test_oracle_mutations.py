@@ -3,7 +3,7 @@
 index or sign, a dropped or wrong Runge-Kutta term, the pump on the wrong mode, a wrong
 normalisation, a wrong mode band, a wrong step in the adjoint), compiles it with the oracle's
 own flags, and runs the committed pin suites (test_oracle_pins, test_oracle_adjoint,
-test_oracle_padding) in a child process whose oracle calls all go to the modified build.  The
+test_oracle_padding, test_oracle_kerr) in a child process whose oracle calls all go to the modified build.  The
 same is done for the oracle's numpy Eq. 4 engine (`oracle/fft_engine.py`) through a copy of the
 package.  The unmodified sources must pass the pins; every mutant must fail at least one.
 CPU only."""
@@ -16,7 +16,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "cme_oracle.c")
 PIN_SUITES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py",
-              "tests/test_oracle_padding.py"]
+              "tests/test_oracle_padding.py", "tests/test_oracle_kerr.py"]
 
 # name: (text in cme_oracle.c, replacement); the text occurs exactly once.
 MUTATIONS = {
@@ -32,7 +32,13 @@ MUTATIONS = {
     # right-hand side and linear operator
     "detuning sign": ("m->omega[i] - omega0 - m->sigma", "m->omega[i] - omega0 + m->sigma"),
     "loss sign": ("return -0.5 * m->kappa[i] + I", "return 0.5 * m->kappa[i] + I"),
-    "Kerr coefficient not imaginary": ("out[i] *= I * m->g0;", "out[i] *= m->g0;"),
+    "Kerr coefficient not imaginary": ("out[i] *= I * kerr_coef(m, i);",
+                                       "out[i] *= kerr_coef(m, i);"),
+    "per-mode Kerr coefficient ignored": ("return m->g0mu ? m->g0mu[i] : m->g0;",
+                                          "return m->g0;"),
+    "per-mode Kerr coefficient of the mirrored mode": (
+        "return m->g0mu ? m->g0mu[i] : m->g0;",
+        "return m->g0mu ? m->g0mu[m->N - 1 - i] : m->g0;"),
     "pump on the wrong mode": ("out[m->N / 2] += sqrt", "out[m->N / 2 + 1] += sqrt"),
     "pump without sqrt(kappa_ext)": ("out[m->N / 2] += sqrt(m->kappa_ext) * m->A_in;",
                                      "out[m->N / 2] += m->kappa_ext * m->A_in;"),
@@ -66,8 +72,8 @@ MUTATIONS = {
                               "s += w * D[beta + h] * conj(D[i]);"),
     "VJP: conjugate dropped on the cotangent": ("s += conj(w) * D[i] * D[gamma + h];",
                                                 "s += w * D[i] * D[gamma + h];"),
-    "adjoint: Kerr coefficient not conjugated": ("tmp[i] = conj(I * m->g0) * ybar[i];",
-                                                 "tmp[i] = (I * m->g0) * ybar[i];"),
+    "adjoint: Kerr coefficient not conjugated": ("tmp[i] = conj(I * kerr_coef(m, i)) * ybar[i];",
+                                                 "tmp[i] = (I * kerr_coef(m, i)) * ybar[i];"),
     "adjoint: k3 cotangent": ("kb[i] = h / 3.0 * wb[i] + h * vb[i];",
                               "kb[i] = h / 3.0 * wb[i] + 0.5 * h * vb[i];"),
     "adjoint: log10 derivative": ("2.0 * r / ((P + eps) * log(10.0));", "2.0 * r / (P + eps);"),
@@ -89,6 +95,8 @@ MUTATIONS = {
                                                          "(e[c0] - phi) / L0"),
     "Strang adjoint: propagator cotangent over h": ("cplx Lb = conj(dt * e[i]) * Eb[i];",
                                                     "cplx Lb = conj(h * e[i]) * Eb[i];"),
+    "Strang adjoint: log10 derivative": ("2.0 * r / (log(10.0) * (P + eps));",
+                                         "2.0 * r / (P + eps);"),
     "Strang adjoint: padding modes in the Kerr cotangent": (
         "tmp[i] = physical(i, N, M) ? Db[i] : 0.0;", "tmp[i] = Db[i];"),
 }
@@ -141,8 +149,11 @@ ENGINE_MUTATIONS = {
     "engine RK4IP: missing propagator on the last stage": (
         "k4 = batch.F(E * (AI + h * k3), linear)", "k4 = batch.F(AI + h * k3, linear)"),
     "engine Strang: half the Kerr phase": (
-        "a = a * np.exp(1j * batch.g0 * np.abs(a) ** 2 * h)",
-        "a = a * np.exp(1j * batch.g0 * np.abs(a) ** 2 * 0.5 * h)"),
+        "a = a * np.exp(1j * batch.g0[:, :1] * np.abs(a) ** 2 * h)",
+        "a = a * np.exp(1j * batch.g0[:, :1] * np.abs(a) ** 2 * 0.5 * h)"),
+    "engine: per-mode Kerr coefficient of the mirrored mode": (
+        "else np.asarray(i.g0_mu, dtype=np.float64) for i in instances])",
+        "else np.asarray(i.g0_mu, dtype=np.float64)[::-1] for i in instances])"),
     "engine Strang: pump increment": ("(e[:, N // 2] - 1.0) / np.where", "e[:, N // 2] / np.where"),
 }
 
