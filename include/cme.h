@@ -247,23 +247,37 @@ typedef struct cme_grads {
     double* d_D0;    /* [2*total_modes] cotangent of the field at the start of the call */
 } cme_grads;
 
-/* Run nsteps steps of the batch's integrator from the current field with checkpoints every
- * `segment` steps (0 = ceil(sqrt(nsteps))), evaluate L against the target T (total_modes
- * doubles: log10 powers, centred, host memory), then run the discrete adjoint backwards,
- * recomputing each segment from its checkpoint (the recomputation of the next segment overlaps
- * the backward pass of the current one, on a second stream).  RK4IP: per step the state, the
+/* Run nsteps steps of the batch's integrator from the current field in segments of `segment`
+ * steps (0 = ceil(sqrt(nsteps))), evaluate L against the target T (total_modes doubles: log10
+ * powers, centred, host memory), then run the discrete adjoint backwards over the segments.
+ * Two schedules:
+ *   - stored trajectory, where the per-step data of the whole run fit the budget of
+ *     cme_set_grad_memory (by default half the device memory free at the call): the forward
+ *     pass stores them as it goes, and the backward pass reads them back; nothing is
+ *     recomputed (N = 4096 x 16 instances, 10000 FP32 steps: 42 GB, FP64: 84 GB);
+ *   - otherwise checkpoints at the segment starts; each segment is recomputed from its
+ *     checkpoint, the recomputation of the next segment overlapping the backward pass of the
+ *     current one on a second stream (sqrt(nsteps) checkpointing).
+ * Both give the same gradient to rounding (the launch plans may differ: the stored schedule's
+ * backward kernel has the GPU to itself).  RK4IP: per step the state, the
  * three stage values and the time-domain fields of the four stage inputs are recomputed, and
  * the backward pass runs four vector-Jacobian products of the right-hand side.  Strang: the
  * state, the time-domain field of the Kerr flow and the state after it are recomputed, and the
  * backward pass runs the exact Kerr flow's vector-Jacobian product (two transforms) between the
  * two linear half flows; the pump increment (exp(L_0 h/2) - 1)/L_0 sqrt(kappa_ext) A_in passes
  * its cotangent to A_in and to L_0.  The batch ends at the final field (tau advanced by
- * h nsteps).  Scratch memory -- ceil(nsteps/segment) checkpoints and the states plus stage
- * values of two segments, 8 * segment field vectors -- is allocated on the first call and kept
- * with the batch.  N <= 4096 only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM, TIMEOUT (a
+ * h nsteps).  Scratch memory -- the stored trajectory, 8 field vectors per step, or
+ * ceil(nsteps/segment) checkpoints and 8 * segment field vectors per segment for two segments --
+ * is allocated on the first call and kept with the batch (and reallocated when a later call
+ * needs more).  N <= 4096 only.  Synchronises.  Errors: INVALID_ARG, CUDA, OOM, TIMEOUT (a
  * bounded wait of a cluster all-to-all gave up). */
 int cme_grad(cme_batch b, double h, long nsteps, const double* target, double eps, long segment,
              cme_grads* out);
+
+/* Budget in bytes for cme_grad's stored trajectory: -1 (default) = half the device memory
+ * free at each call, 0 = never store (always checkpoint and recompute), > 0 = store when the
+ * trajectory needs at most max_bytes.  Errors: INVALID_ARG. */
+int cme_set_grad_memory(cme_batch b, long long max_bytes);
 
 /* ---- hot-path pieces, for testing ----------------------------------------------------- */
 

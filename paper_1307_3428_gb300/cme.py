@@ -91,6 +91,7 @@ _SIGS = [
     ("cme_debug_fault", ctypes.c_int, [_VP, ctypes.c_int]),
     ("cme_grad", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_long, _DP, ctypes.c_double,
                                 ctypes.c_long, ctypes.POINTER(Grads)]),
+    ("cme_set_grad_memory", ctypes.c_int, [_VP, ctypes.c_longlong]),
     ("cme_rk4ip_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_long, _VP, _VP, _VP, _VP, _VP]),
     ("cme_transform", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int]),
@@ -363,6 +364,11 @@ class Batch:
         out["d_A_in"] = out["d_A_in"].view(np.complex128)
         out["d_D0"] = out["d_D0"].view(np.complex128)
         return out
+
+    def set_grad_memory(self, max_bytes: int):
+        """cme_set_grad_memory: budget of the stored-trajectory gradient (-1 automatic, 0 never:
+        checkpoint and recompute)."""
+        _check(load().cme_set_grad_memory(self.handle, int(max_bytes)))
 
     def eval_rhs(self) -> np.ndarray:
         out = np.empty(2 * self.total, dtype=np.float64)

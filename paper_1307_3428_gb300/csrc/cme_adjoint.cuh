@@ -125,10 +125,9 @@ CME_HD constexpr size_t adj_backward_smem()
            (adj_prefetch<T, LOGN, R, C>() ? adj_prefetch_bytes<T, LOGN, R, C>() + 16 : 0);
 }
 
-// Recompute role: the states of segment A.seg from its checkpoint and, for every step, into
-// half (A.seg mod 2) of A.stages: RK4IP, the stage values y1, k2, k3 and the time-domain fields
-// of the four stage inputs; Strang, the time-domain field of the Kerr flow and the state after
-// it.
+// Recompute role: the states of segment A.seg from checkpoint A.ckpt_slot and, for every step,
+// into slot A.slot of A.stages: RK4IP, the stage values y1, k2, k3 and the time-domain fields of
+// the four stage inputs; Strang, the time-domain field of the Kerr flow and the state after it.
 template <typename T, int LOGN, int R, int C = 1, int METHOD = METHOD_RK4IP>
 __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(const AdjArgs A)
 {
@@ -148,13 +147,13 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
     pr.init(a, off, t);
     const long long TT = A.total, s = A.seg;
     const long long ns = (A.nsteps - s * A.K < A.K) ? A.nsteps - s * A.K : A.K;
-    fs.load(reinterpret_cast<const cx<T>*>(A.ckpt_hi) + s * TT + off + t,
-            reinterpret_cast<const cx<T>*>(A.ckpt_lo) + s * TT + off + t);
+    fs.load(reinterpret_cast<const cx<T>*>(A.ckpt_hi) + A.ckpt_slot * TT + off + t,
+            reinterpret_cast<const cx<T>*>(A.ckpt_lo) + A.ckpt_slot * TT + off + t);
     // this thread's slots of step 0 of the segment (surplus groups of a packed block recompute
     // the last instance for the barriers and store nothing); the stage buffer is private to
     // the two roles, so it is indexed by the coalesced scratch slot ts
     cx<T>* out =
-        reinterpret_cast<cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + grp.ts;
+        reinterpret_cast<cx<T>*>(A.stages) + A.slot * A.K * ADJ_VECS * TT + off + grp.ts;
     if constexpr (C > 1)
         cluster_sync();   // every block of the cluster runs before the first remote store
     for (long long i = 0; i < ns; ++i) {
@@ -169,6 +168,11 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
         else
             strang_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
     }
+    // a gradient whose whole trajectory is stored runs its forward pass through this kernel:
+    // the segment's final state starts the next segment (or is the final field)
+    if (A.out_hi && valid)
+        fs.store(reinterpret_cast<cx<T>*>(A.out_hi) + off + t,
+                 reinterpret_cast<cx<T>*>(A.out_lo) + off + t);
     if (grp.failed() && a.status)
         a.status[inst] = 2;
     if constexpr (C > 1)
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
     const long long TT = A.total, s = A.seg;
     const long long ns = (A.nsteps - s * A.K < A.K) ? A.nsteps - s * A.K : A.K;
     const cx<T>* buf =
-        reinterpret_cast<const cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + grp.ts;
+        reinterpret_cast<const cx<T>*>(A.stages) + A.slot * A.K * ADJ_VECS * TT + off + grp.ts;
     cx<T>* dbp = reinterpret_cast<cx<T>*>(A.dbar) + off + t;
     double2* glp = A.gL + off + t;
 
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) strang_adjoint_kern
     const long long TT = A.total, s = A.seg;
     const long long ns = (A.nsteps - s * A.K < A.K) ? A.nsteps - s * A.K : A.K;
     const cx<T>* buf =
-        reinterpret_cast<const cx<T>*>(A.stages) + (s & 1) * A.K * ADJ_VECS * TT + off + grp.ts;
+        reinterpret_cast<const cx<T>*>(A.stages) + A.slot * A.K * ADJ_VECS * TT + off + grp.ts;
     cx<T>* dbp = reinterpret_cast<cx<T>*>(A.dbar) + off + t;
     double2* glp = A.gL + off + t;
 

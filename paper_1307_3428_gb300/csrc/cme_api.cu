@@ -211,7 +211,9 @@ struct cme_batch_s {
     std::vector<double> sqk_h;        // sqrt(kappa_ext) per instance
 
     // gradient scratch (allocated by the first cme_grad call, grown when needed)
-    long long g_S = 0, g_K = 0;
+    long long g_S = 0, g_K = 0;      // checkpoints and steps per segment the scratch holds
+    long long g_slots = 0;           // segments of per-step data the scratch holds
+    long long grad_budget = -1;      // cme_set_grad_memory: -1 automatic, 0 never store
     void *g_ckpt_hi = nullptr, *g_ckpt_lo = nullptr, *g_stages = nullptr, *g_dbar = nullptr;
     cudaStream_t g_side = nullptr;              // recomputation stream of cme_grad
     cudaEvent_t g_ev[4] = {};                   // fork, recomputed, backward done (x2)
@@ -825,16 +827,11 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     if (b->groups.size() > 1) {
         b->side.resize(b->groups.size());
         b->ev.resize(b->groups.size() + 1);
-        // The largest N's side stream gets the highest priority, the others the lowest: the
-        // block scheduler then places all of its blocks (one per SM for N = 4096, which needs
-        // most of an SM's shared memory) before the lighter groups' blocks, which could
-        // otherwise occupy those SMs first and delay the group that sets the run time (the
-        // uneven N = 256 ... 4096 batch measured 584 and 635 ms per run without priorities).
-        int least = 0, greatest = 0;
-        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        for (size_t i = 0; e == cudaSuccess && i < b->side.size(); ++i)
-            e = cudaStreamCreateWithPriority(&b->side[i], cudaStreamNonBlocking,
-                                             i + 1 == b->side.size() ? greatest : least);
+        for (auto& st : b->side) {
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e != cudaSuccess)
+                break;
+        }
         for (auto& ev : b->ev) {
             if (e == cudaSuccess)
                 e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -1708,9 +1705,10 @@ int cme_fma_peak(int precision, double* flops_per_s)
 
 namespace {
 
-int ensure_grad_scratch(cme_batch b, long long S, long long K)
+// Gradient scratch: `S` checkpoints and `slots` segments of K steps of per-step data.
+int ensure_grad_scratch(cme_batch b, long long S, long long slots, long long K)
 {
-    if (b->g_S >= S && b->g_K >= K && !b->g_allocs.empty())
+    if (b->g_S >= S && b->g_K >= K && b->g_slots >= slots && !b->g_allocs.empty())
         return CME_OK;
     for (void* p : b->g_allocs)
         dev_free(p, b->free_fn, b->free_ctx);
@@ -1727,7 +1725,7 @@ int ensure_grad_scratch(cme_batch b, long long S, long long K)
     };
     b->g_ckpt_hi = A(S * T * E);
     b->g_ckpt_lo = b->prec == PREC_FP32 ? A(S * T * E) : nullptr;
-    b->g_stages = A(2 * K * ADJ_VECS * T * E);
+    b->g_stages = A(slots * K * ADJ_VECS * T * E);
     b->g_dbar = A(T * E);
     b->g_gL = (double2*)A(T * 16);
     b->g_pbar = (double2*)A(C * 16);
@@ -1741,9 +1739,10 @@ int ensure_grad_scratch(cme_batch b, long long S, long long K)
         for (void* p : b->g_allocs)
             dev_free(p, b->free_fn, b->free_ctx);
         b->g_allocs.clear();
-        b->g_S = b->g_K = 0;
-        return fail(CME_ERR_OOM, "cme_grad: cannot allocate %lld checkpoints x %lld modes", S,
-                    (long long)T);
+        b->g_S = b->g_K = b->g_slots = 0;
+        return fail(CME_ERR_OOM,
+                    "cme_grad: cannot allocate %lld checkpoints and %lld segments of %lld steps x "
+                    "%lld modes", S, slots, K, (long long)T);
     }
     if (!b->g_side) {
         cudaError_t e = cudaStreamCreateWithFlags(&b->g_side, cudaStreamNonBlocking);
@@ -1755,10 +1754,19 @@ int ensure_grad_scratch(cme_batch b, long long S, long long K)
     }
     b->g_S = S;
     b->g_K = K;
+    b->g_slots = slots;
     return CME_OK;
 }
 
 }  // namespace
+
+extern "C" int cme_set_grad_memory(cme_batch b, long long max_bytes)
+{
+    if (!b)
+        return fail(CME_ERR_INVALID_ARG, "cme_set_grad_memory: NULL batch");
+    b->grad_budget = max_bytes < 0 ? -1 : max_bytes;
+    return CME_OK;
+}
 
 extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target, double eps,
                         long segment, cme_grads* out)
@@ -1770,7 +1778,30 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
         return fail(CME_ERR_INVALID_ARG, "cme_grad: gradients are implemented for N <= 4096");
     const long long K = segment ? segment : (long long)std::ceil(std::sqrt((double)nsteps));
     const long long S = (nsteps + K - 1) / K;
-    int rc = ensure_grad_scratch(b, S, K);
+    // Stored trajectory: when the per-step data of all S segments fit the budget
+    // (cme_set_grad_memory; by default half the free device memory), the forward pass itself
+    // stores them, segment by segment through the recomputation kernel, and the backward pass
+    // reads them without recomputing anything.  Otherwise checkpoints every K steps, and each
+    // segment is recomputed from its checkpoint on a second stream while the next one runs
+    // backwards.
+    const size_t slot_bytes = (size_t)K * ADJ_VECS * (size_t)b->total * b->elem;
+    bool stored = false;
+    if (b->grad_budget != 0) {
+        size_t budget = (size_t)b->grad_budget;
+        if (b->grad_budget < 0) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+                cudaGetLastError();
+                fr = 0;
+            }
+            // scratch this batch already holds is free for this call
+            const size_t held = (size_t)b->g_slots * (size_t)b->g_K * ADJ_VECS *
+                                (size_t)b->total * b->elem;
+            budget = (fr + held) / 2;
+        }
+        stored = (size_t)S * slot_bytes <= budget;
+    }
+    int rc = stored ? ensure_grad_scratch(b, 2, S, K) : ensure_grad_scratch(b, S, 2, K);
     if (rc)
         return rc;
     rc = ensure_propagators(b, h);
@@ -1792,9 +1823,11 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
         if (b->prec != PREC_FP32 || g.large)
             continue;
         if (b->opt.cluster == 0 && (g.logN == 11 || g.logN == 12)) {
+            // with a stored trajectory the backward kernel runs alone: the whole GPU is its
+            const long long share = stored ? 1 : 2;
             g.C = 1;
             for (int c : {8, 4})
-                if (cluster_shape_compiled(g.logN, 8, c) && 2LL * g.count * c <= b->sms) {
+                if (cluster_shape_compiled(g.logN, 8, c) && share * g.count * c <= b->sms) {
                     g.C = c;
                     break;
                 }
@@ -1807,31 +1840,11 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
             g.G = 1;
         }
     }
-    // forward with checkpoints at the segment starts
-    for (long long s = 0; s < S; ++s) {
-        CME_CUDA(cudaMemcpyAsync((char*)b->g_ckpt_hi + s * fb, b->hi, fb, cudaMemcpyDeviceToDevice, st),
-                 "cme_grad: checkpoint");
-        if (b->prec == PREC_FP32)
-            CME_CUDA(cudaMemcpyAsync((char*)b->g_ckpt_lo + s * fb, b->lo, fb,
-                                     cudaMemcpyDeviceToDevice, st),
-                     "cme_grad: checkpoint");
-        const long long n = std::min(K, (long long)nsteps - s * K);
-        for (auto& g : ag)
-            CME_CUDA(launch_group_step(b, g, n, st), "cme_grad: forward");
-    }
-    // loss and its seed
-    CME_CUDA(cudaMemcpyAsync(b->g_target, target, (size_t)b->total * 8, cudaMemcpyHostToDevice, st),
-             "cme_grad: target");
-    ++g_launches;
-    CME_CUDA(launch_loss_seed(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, b->hi,
-                              b->lo, b->g_target, eps, b->g_loss, b->g_dbar, st),
-             "cme_grad: seed");
-    // backward: segments in reverse.  The recomputation of segment s (states and stage values,
-    // independent of every cotangent) runs on the side stream into half s mod 2 of the stage
-    // buffer while segment s + 1 runs backwards on the batch stream from the other half.
-    CME_CUDA(cudaMemsetAsync(b->g_gL, 0, (size_t)b->total * 16, st), "cme_grad: zero");
-    CME_CUDA(cudaMemsetAsync(b->g_pbar, 0, (size_t)b->count * 16, st), "cme_grad: zero");
-    auto run_segment = [&](int role, long long sg, cudaStream_t str) -> cudaError_t {
+    // One launch per group of the recomputation (ADJ_RECOMPUTE) or backward role for segment sg,
+    // its per-step data in slot `slot`; the recomputation starts from checkpoint `ckpt` and,
+    // where out_hi is set, leaves its final state there.
+    auto run_segment = [&](int role, long long sg, long long slot, long long ckpt, void* out_hi,
+                           void* out_lo, cudaStream_t str) -> cudaError_t {
         for (const auto& ga : ag) {
             AdjArgs A{};
             A.s = group_args(b, ga);
@@ -1847,6 +1860,10 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
             A.gL = b->g_gL;
             A.pbar = b->g_pbar + ga.first;
             A.method = b->method;
+            A.slot = slot;
+            A.ckpt_slot = ckpt;
+            A.out_hi = out_hi;
+            A.out_lo = out_lo ? out_lo : out_hi;
             ++g_launches;
             cudaError_t e = b->prec == PREC_FP64
                                 ? launch_adjoint_fp64(role, ga.logN, ga.R, ga.C, A, str)
@@ -1856,22 +1873,76 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
         }
         return cudaSuccess;
     };
-    cudaEvent_t ev_fork = b->g_ev[0], ev_rec = b->g_ev[1], ev_back[2] = {b->g_ev[2], b->g_ev[3]};
-    cudaStream_t side = b->g_side;
-    CME_CUDA(cudaEventRecord(ev_fork, st), "cme_grad: fork");
-    CME_CUDA(cudaStreamWaitEvent(side, ev_fork, 0), "cme_grad: fork");
-    CME_CUDA(run_segment(ADJ_RECOMPUTE, S - 1, side), "cme_grad: recompute");
-    CME_CUDA(cudaEventRecord(ev_rec, side), "cme_grad: recompute");
-    for (long long sg = S - 1; sg >= 0; --sg) {
-        CME_CUDA(cudaStreamWaitEvent(st, ev_rec, 0), "cme_grad: join");
-        CME_CUDA(run_segment(ADJ_BACKWARD, sg, st), "cme_grad: adjoint kernel");
-        CME_CUDA(cudaEventRecord(ev_back[sg & 1], st), "cme_grad: backward");
-        if (sg >= 1) {
-            // half (sg - 1) mod 2 was last read by the backward pass of segment sg + 1
-            if (sg + 1 <= S - 1)
-                CME_CUDA(cudaStreamWaitEvent(side, ev_back[(sg + 1) & 1], 0), "cme_grad: wait");
-            CME_CUDA(run_segment(ADJ_RECOMPUTE, sg - 1, side), "cme_grad: recompute");
-            CME_CUDA(cudaEventRecord(ev_rec, side), "cme_grad: recompute");
+    if (stored) {
+        // forward through the recomputation kernel: segment s starts from checkpoint s mod 2
+        // and leaves its final state in the other one (the last in the batch's field)
+        CME_CUDA(cudaMemcpyAsync(b->g_ckpt_hi, b->hi, fb, cudaMemcpyDeviceToDevice, st),
+                 "cme_grad: checkpoint");
+        if (b->prec == PREC_FP32)
+            CME_CUDA(cudaMemcpyAsync(b->g_ckpt_lo, b->lo, fb, cudaMemcpyDeviceToDevice, st),
+                     "cme_grad: checkpoint");
+        for (long long sg = 0; sg < S; ++sg) {
+            const long long nx = (sg + 1) & 1;
+            void* oh = sg + 1 == S ? b->hi : (char*)b->g_ckpt_hi + nx * fb;
+            void* ol = sg + 1 == S ? b->lo
+                                   : (b->g_ckpt_lo ? (char*)b->g_ckpt_lo + nx * fb : nullptr);
+            CME_CUDA(run_segment(ADJ_RECOMPUTE, sg, sg, sg & 1, oh, ol, st), "cme_grad: forward");
+        }
+    } else {
+        // forward with checkpoints at the segment starts
+        for (long long s = 0; s < S; ++s) {
+            CME_CUDA(cudaMemcpyAsync((char*)b->g_ckpt_hi + s * fb, b->hi, fb,
+                                     cudaMemcpyDeviceToDevice, st),
+                     "cme_grad: checkpoint");
+            if (b->prec == PREC_FP32)
+                CME_CUDA(cudaMemcpyAsync((char*)b->g_ckpt_lo + s * fb, b->lo, fb,
+                                         cudaMemcpyDeviceToDevice, st),
+                         "cme_grad: checkpoint");
+            const long long n = std::min(K, (long long)nsteps - s * K);
+            for (auto& g : ag)
+                CME_CUDA(launch_group_step(b, g, n, st), "cme_grad: forward");
+        }
+    }
+    // loss and its seed
+    CME_CUDA(cudaMemcpyAsync(b->g_target, target, (size_t)b->total * 8, cudaMemcpyHostToDevice, st),
+             "cme_grad: target");
+    ++g_launches;
+    CME_CUDA(launch_loss_seed(b->prec, (int)b->total, b->mode_inst, b->inst_N, b->inst_off, b->hi,
+                              b->lo, b->g_target, eps, b->g_loss, b->g_dbar, st),
+             "cme_grad: seed");
+    // backward: segments in reverse.  Stored trajectory: each segment reads its own slot.
+    // Otherwise the recomputation of segment s (states and stage values, independent of every
+    // cotangent) runs on the side stream into slot s mod 2 of the stage buffer while segment
+    // s + 1 runs backwards on the batch stream from the other slot.
+    CME_CUDA(cudaMemsetAsync(b->g_gL, 0, (size_t)b->total * 16, st), "cme_grad: zero");
+    CME_CUDA(cudaMemsetAsync(b->g_pbar, 0, (size_t)b->count * 16, st), "cme_grad: zero");
+    if (stored) {
+        for (long long sg = S - 1; sg >= 0; --sg)
+            CME_CUDA(run_segment(ADJ_BACKWARD, sg, sg, 0, nullptr, nullptr, st),
+                     "cme_grad: adjoint kernel");
+    } else {
+        cudaEvent_t ev_fork = b->g_ev[0], ev_rec = b->g_ev[1],
+                    ev_back[2] = {b->g_ev[2], b->g_ev[3]};
+        cudaStream_t side = b->g_side;
+        CME_CUDA(cudaEventRecord(ev_fork, st), "cme_grad: fork");
+        CME_CUDA(cudaStreamWaitEvent(side, ev_fork, 0), "cme_grad: fork");
+        CME_CUDA(run_segment(ADJ_RECOMPUTE, S - 1, (S - 1) & 1, S - 1, nullptr, nullptr, side),
+                 "cme_grad: recompute");
+        CME_CUDA(cudaEventRecord(ev_rec, side), "cme_grad: recompute");
+        for (long long sg = S - 1; sg >= 0; --sg) {
+            CME_CUDA(cudaStreamWaitEvent(st, ev_rec, 0), "cme_grad: join");
+            CME_CUDA(run_segment(ADJ_BACKWARD, sg, sg & 1, sg, nullptr, nullptr, st),
+                     "cme_grad: adjoint kernel");
+            CME_CUDA(cudaEventRecord(ev_back[sg & 1], st), "cme_grad: backward");
+            if (sg >= 1) {
+                // half (sg - 1) mod 2 was last read by the backward pass of segment sg + 1
+                if (sg + 1 <= S - 1)
+                    CME_CUDA(cudaStreamWaitEvent(side, ev_back[(sg + 1) & 1], 0), "cme_grad: wait");
+                CME_CUDA(run_segment(ADJ_RECOMPUTE, sg - 1, (sg - 1) & 1, sg - 1, nullptr, nullptr,
+                                     side),
+                         "cme_grad: recompute");
+                CME_CUDA(cudaEventRecord(ev_rec, side), "cme_grad: recompute");
+            }
         }
     }
     if (b->method == METHOD_STRANG) {

@@ -411,3 +411,46 @@ def test_strang_fp32_adjoint_close_to_fp64():
         assert np.max(np.abs(a - b)) <= (1e-3 if N <= 512 else 1e-2) * np.max(np.abs(b))
         assert np.linalg.norm(g32["d_D0"] - g64["d_D0"]) <= 1e-3 * np.linalg.norm(g64["d_D0"])
         assert np.max(np.abs(g32["loss"] - g64["loss"])) <= 1e-5 * np.max(np.abs(g64["loss"]))
+
+
+def test_strang_cluster_adjoint_agrees_with_one_block():
+    """The Strang backward kernel on 4- and 8-block clusters (N = 2048, 4096) against one block
+    per instance, FP64: the same gradient to 1e-9."""
+    for N, C in ((2048, 4), (4096, 8)):
+        insts = [wl.make_instance(N, 0.01, 1e-4, 2.0 + k, 2.0, 1e-3, seed=230 + k)
+                 for k in range(2)]
+        T = np.concatenate([target_for(N, 240 + k) for k in range(2)])
+        g = {}
+        for c in (1, C):
+            b = cme.Batch([cme.Instance.from_workload(i) for i in insts], precision=cme.FP64,
+                          integrator=cme.STRANG, radix=8, cluster=c)
+            g[c] = b.grad(2e-4, 30, T, segment=7)
+            b.close()
+        for key in g[1]:
+            a, r = np.asarray(g[C][key]), np.asarray(g[1][key])
+            assert np.linalg.norm(a - r) <= 1e-9 * np.linalg.norm(r), (N, key)
+
+
+@pytest.mark.parametrize("integ", [cme.RK4IP, cme.STRANG])
+@pytest.mark.parametrize("prec", [cme.FP64, cme.FP32])
+def test_stored_and_recomputed_schedules_agree(prec, integ):
+    """cme_grad stores the whole trajectory where it fits the budget (cme_set_grad_memory, by
+    default half the free device memory) and otherwise checkpoints and recomputes segments on
+    a second stream.  With the same launch plan both run the same arithmetic in the same
+    order: the gradients are identical, on one block per instance (N = 64, segments of 5
+    steps over 37) and on 4-block clusters (N = 4096, whose FP32 backward kernel prefetches)."""
+    for N, kw in ((64, {}), (4096, {"cluster": 4, "radix": 8})):
+        insts = [wl.make_instance(N, 0.01, 1e-4, 1.5 + k, 2.0, 1e-3, seed=250 + k)
+                 for k in range(2)]
+        T = np.concatenate([target_for(N, 260 + k) for k in range(2)])
+        out = {}
+        for budget in (-1, 0):
+            b = cme.Batch([cme.Instance.from_workload(i) for i in insts], precision=prec,
+                          integrator=integ, **kw)
+            b.set_grad_memory(budget)
+            out[budget] = b.grad(5e-4, 37, T, segment=5)
+            fin = b.get_state()
+            b.close()
+            out[budget]["final"] = fin
+        for key in out[0]:
+            assert np.array_equal(out[-1][key], out[0][key]), (N, key)
