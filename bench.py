@@ -16,6 +16,8 @@ Extra measurements on the same JSON line:
   e2e       the same metric through the C ABI with host buffers (H2D of the initial field from
             pinned memory and D2H of the power spectrum inside the timed region);
   cpu_baseline  the FP64 CPU oracle (direct O(N^3) sum) on a bounded sample.
+  other_workloads  (one GPU) the uneven, octave, N=4096 forward, Strang and Fig. 1 workloads
+            and the N=4096 gradient in both precisions, each timed beside the headline.
 
 `--impl reference` times the CPU oracle alone on the same metric (rank 0 only).
 """
@@ -268,8 +270,9 @@ def run_reference(args, world, rank):
 # ------------------------------------------------------------------------------ adjoint
 def run_adjoint(args, world, rank, local):
     """cme_grad on N=4096 x 16 instances, 10000 RK4IP steps, log-spectrum loss against seeded
-    sech^2 targets: forward with sqrt(n) checkpoints plus the discrete adjoint, FP32; the FP64
-    adjoint is timed on a shorter horizon for comparison."""
+    sech^2 targets: forward plus the discrete adjoint in FP32, with the library's choice of
+    schedule (the stored trajectory where it fits) and with sqrt(n) checkpoints; the FP64
+    gradient of the same run, the supported one at this configuration, beside it."""
     import numpy as np
     import torch
 
@@ -289,10 +292,12 @@ def run_adjoint(args, world, rank, local):
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
-    def timed(prec, n, reps, warmup, sampler=None):
+    def timed(prec, n, reps, warmup, sampler=None, budget=-1):
         """Mean device time of `reps` gradients (CUDA events on the batch's stream, L2 flushed
-        before each), after `warmup` untimed ones (the first allocates the scratch)."""
+        before each), after `warmup` untimed ones (the first allocates the scratch), and the
+        schedule the library took (budget: cme_set_grad_memory)."""
         b = cme.Batch(insts, precision=prec, cluster=args.cluster)
+        b.set_grad_memory(budget)
         stream = torch.cuda.ExternalStream(b.stream)
         for _ in range(warmup):
             b.set_state_device(d0.data_ptr())
@@ -312,21 +317,33 @@ def run_adjoint(args, world, rank, local):
             e1.synchronize()
             ts.append(e0.elapsed_time(e1) * 1e-3)
         clocks = sampler.stop() if sampler else None
+        sched = b.last_grad_schedule
         b.close()
-        return sum(ts) / len(ts), g, clocks
+        return sum(ts) / len(ts), g, clocks, sched
 
     launches0 = cme.kernel_launches()
-    t32, g32, clocks = timed(cme.FP32, nsteps, args.steps, args.warmup, ClockSampler(local))
+    t32, g32, clocks, sched32 = timed(cme.FP32, nsteps, args.steps, args.warmup,
+                                      ClockSampler(local))
     launches = (cme.kernel_launches() - launches0) // (args.steps + args.warmup)
     # the FP64 gradient of the same workload, full horizon: the supported gradient of this
     # configuration and the reference of the FP32 gradient's error
-    t64, g64, _ = timed(cme.FP64, nsteps, 1, 1)
+    t64, g64, _, sched64 = timed(cme.FP64, nsteps, 1, 1)
     mode_steps = N * B * nsteps
-    # forward, recomputation and backward: three times the forward step's 8 transforms of
-    # 5 N log2 N flop plus ~80 pointwise flop per mode
-    flops = mode_steps * 3 * (8 * 5 * math.log2(N) + 80)
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+    def grad_flops(sched):
+        """Algorithmic work of one gradient: the forward step's 8 transforms of 5 N log2 N flop
+        plus ~80 pointwise flop per mode-step, once for the forward pass, once for the backward
+        pass (4 vector-Jacobian products of 2 transforms each), and once more for the
+        recomputation of the checkpoint schedule."""
+        return mode_steps * (2 if sched == "stored" else 3) * (8 * 5 * math.log2(N) + 80)
+
+    flops = grad_flops(sched32)
     achieved = flops / t32 / 1e12
+    # the other schedule of the same FP32 gradient, for comparison
+    tck, _, _, schedck = timed(cme.FP32, nsteps, 2, 1, budget=0)
+    assert schedck == "checkpoint"
+    achieved_ck = grad_flops("checkpoint") / tck / 1e12
     rel = lambda a, b: float(np.max(np.abs(np.asarray(a) - np.asarray(b))) /
                              np.max(np.abs(np.asarray(b))))
     line = {
@@ -336,18 +353,30 @@ def run_adjoint(args, world, rank, local):
         "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"adjoint_n4096_b16: N=4096 x 16, {nsteps} RK4IP steps of "
-                               "h=2e-4, sqrt(n) checkpoints, sech^2 log-spectrum targets",
+                               f"h=2e-4, {sched32} schedule, sech^2 log-spectrum targets",
                    "cluster": args.cluster or "library choice",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "clocks": clocks,
+        "schedule": sched32,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "basis": "3 x (8 transforms of 5 N log2 N + 80) flop per mode-step: forward, "
-                              "checkpoint recomputation, backward"},
+                     "basis": ("2 x (8 transforms of 5 N log2 N + 80) flop per mode-step: forward "
+                               "and backward, the stored trajectory recomputing nothing"
+                               if sched32 == "stored" else
+                               "3 x (8 transforms of 5 N log2 N + 80) flop per mode-step: forward, "
+                               "checkpoint recomputation, backward")},
+        "checkpoint_schedule": {
+            "what": "the same FP32 gradient with cme_set_grad_memory(0): sqrt(n) checkpoints, "
+                    "each segment recomputed on a second stream",
+            "value": mode_steps / tck, "ms": tck * 1e3,
+            "roofline": {"bound": "alu", "achieved": achieved_ck, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved_ck / peak,
+                         "basis": "3 x (8 transforms of 5 N log2 N + 80) flop per mode-step"}},
         "fp64": {"value": N * B * nsteps / t64, "steps": nsteps, "ms": t64 * 1e3,
+                 "schedule": sched64,
                  "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
-                              "achieved": flops / t64 / 1e12,
-                              "frac": flops / t64 / 1e12 / FP64_NOMINAL_TFLOPS},
+                              "achieved": grad_flops(sched64) / t64 / 1e12,
+                              "frac": grad_flops(sched64) / t64 / 1e12 / FP64_NOMINAL_TFLOPS},
                  "note": "the FP64 gradient is the supported one at this configuration: the FP32 "
                          "gradients of dL/dD2 and dL/dD3 are dominated by noise-floor modes that "
                          "FP32 transforms do not resolve (error.full_horizon)"},
@@ -421,6 +450,109 @@ def large_source_hash() -> str:
         with open(os.path.join(ROOT, "paper_1307_3428_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------ other workloads
+def other_workloads(cme, wl, torch, flush, reps: int = 2) -> dict:
+    """The other workloads measured beside the headline in the same run (one GPU): each batch on
+    the library's default launch plan, one untimed run (graph capture, scratch allocation), then
+    `reps` runs timed with CUDA events on the batch's stream, L2 flushed before each.  A workload
+    that fails reports its error and leaves the others standing."""
+    import types
+
+    import numpy as np
+    peak32 = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out = {"how": f"library default plan, 1 untimed run, mean of {reps} timed runs (CUDA events "
+                  "on the batch's stream, reset of the field included, L2 flushed before each)"}
+
+    def timed_runs(b, d0, h, n):
+        stream = torch.cuda.ExternalStream(b.stream)
+        b.set_state_device(d0.data_ptr())
+        b.step(h, n)
+        b.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.set_state_device(d0.data_ptr())
+            b.step(h, n)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    def forward(name, w, integ=cme.RK4IP, flop_fn=None, large=False):
+        try:
+            insts = [cme.Instance.from_workload(i) for i in w.instances]
+            b = cme.Batch(insts, precision=cme.FP32, integrator=integ, use_graph=True)
+            D0 = np.concatenate([i.D0 for i in w.instances])
+            d0 = torch.from_numpy(D0.view(np.float64).copy()).cuda()
+            ms = timed_runs(b, d0, w.h, w.nsteps)
+            sizes = [i.N for i in w.instances]
+            ent = {"workload": w.name, "value": sum(sizes) * w.nsteps / (ms * 1e-3),
+                   "unit": UNIT, "ms_per_run": ms, "steps": w.nsteps, "instances": len(sizes),
+                   "dtype": "f32", "launch_plan": b.plan(0)}
+            if flop_fn is not None:
+                f = sum(n * flop_fn(n) for n in sizes) * w.nsteps / (ms * 1e-3) / 1e12
+                ent["roofline"] = {"bound": "alu", "achieved": f, "peak": peak32,
+                                   "unit": "TFLOP/s", "frac": f / peak32}
+            if large:
+                alu = ent.pop("roofline")
+                ent["roofline"] = large_n_roofline(types.SimpleNamespace(radix=0), sizes,
+                                                   w.nsteps, ms, cme, alu)
+            b.close()
+            out[name] = ent
+        except Exception as e:   # context beside the headline: the line stands without it
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    forward("uneven", wl.uneven(), flop_fn=flops_per_mode_step)
+    forward("octave", wl.octave(), flop_fn=flops_per_mode_step, large=True)
+    forward("forward4096", wl.adjoint4096(), flop_fn=flops_per_mode_step)
+    forward("strang_sweep512", wl.sweep512(), integ=cme.STRANG,
+            flop_fn=lambda n: 10.0 * math.log2(n) + 40.0)
+    forward("fig1", wl.fig1(), integ=cme.STRANG)
+
+    # the gradient workload: N = 4096 x 16, 10000 steps, both precisions, library schedule
+    try:
+        w = wl.adjoint4096()
+        N, B = 4096, len(w.instances)
+        T = wl.sech2_target(N, B).reshape(-1)
+        insts = [cme.Instance.from_workload(i) for i in w.instances]
+        D0 = np.concatenate([i.D0 for i in w.instances])
+        d0 = torch.from_numpy(D0.view(np.float64).copy()).cuda()
+        for prec, key in ((cme.FP32, "adjoint_fp32"), (cme.FP64, "adjoint_fp64")):
+            b = cme.Batch(insts, precision=prec)
+            stream = torch.cuda.ExternalStream(b.stream)
+            b.set_state_device(d0.data_ptr())
+            b.grad(w.h, w.nsteps, T)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.set_state_device(d0.data_ptr())
+            b.grad(w.h, w.nsteps, T)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            sched = b.last_grad_schedule
+            b.close()
+            f = (N * B * w.nsteps * (2 if sched == "stored" else 3) *
+                 (8 * 5 * math.log2(N) + 80) / (ms * 1e-3) / 1e12)
+            pk = peak32 if prec == cme.FP32 else FP64_NOMINAL_TFLOPS
+            out[key] = {"workload": w.name, "value": N * B * w.nsteps / (ms * 1e-3),
+                        "unit": "gradient mode-steps/s", "ms_per_gradient": ms,
+                        "steps": w.nsteps, "schedule": sched,
+                        "dtype": "f32" if prec == cme.FP32 else "f64",
+                        "roofline": {"bound": "alu", "achieved": f, "peak": pk,
+                                     "unit": "TFLOP/s", "frac": f / pk},
+                        "timed": "1 untimed gradient, then 1 timed"}
+    except Exception as e:
+        out["adjoint"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 # ------------------------------------------------------------------------------ GPU arm
@@ -651,6 +783,10 @@ def run_gpu(args, world, rank, local):
     e2e = {"value": world * mode_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(host_in.nbytes), "d2h_bytes_per_step": int(spec.nbytes)}
 
+    others = None
+    if headline and world == 1 and not args.skip_others:
+        others = other_workloads(cme, wl, torch, flush)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -671,6 +807,8 @@ def run_gpu(args, world, rank, local):
         "wall_s_timed": wall,
         "gather": gather,
     }
+    if others is not None:
+        line["other_workloads"] = others
     if retimed:
         line["retimed_after_low_fma_rate"] = True
     if plan is not None:
@@ -761,6 +899,8 @@ def main():
     ap.add_argument("--strang", action="store_true", help="Strang split step instead of RK4IP")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-others", action="store_true",
+                    help="leave out the other workloads measured beside the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

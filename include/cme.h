@@ -245,6 +245,8 @@ typedef struct cme_grads {
     double* d_omega; /* [total_modes] dL/domega_mu */
     double* d_kappa; /* [total_modes] dL/dkappa_mu */
     double* d_D0;    /* [2*total_modes] cotangent of the field at the start of the call */
+    int stored;      /* out: 1 if the call stored the whole trajectory, 0 if it checkpointed and
+                        recomputed segments (see cme_grad) */
 } cme_grads;
 
 /* Run nsteps steps of the batch's integrator from the current field in segments of `segment`

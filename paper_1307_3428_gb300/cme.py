@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
 
 class Grads(ctypes.Structure):
     _fields_ = [(n, ctypes.POINTER(ctypes.c_double)) for n in
-                ("loss", "d_sigma", "d_A_in", "d_D2", "d_D3", "d_omega", "d_kappa", "d_D0")]
+                ("loss", "d_sigma", "d_A_in", "d_D2", "d_D3", "d_omega", "d_kappa", "d_D0")] + \
+               [("stored", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -361,6 +362,8 @@ class Batch:
         g = Grads(**{k: _dptr(v) for k, v in out.items()})
         _check(load().cme_grad(self.handle, float(h), int(nsteps), _dptr(T), float(eps),
                                int(segment), ctypes.byref(g)))
+        # which schedule the library chose: "stored" trajectory or "checkpoint" and recompute
+        self.last_grad_schedule = "stored" if g.stored else "checkpoint"
         out["d_A_in"] = out["d_A_in"].view(np.complex128)
         out["d_D0"] = out["d_D0"].view(np.complex128)
         return out

@@ -1989,6 +1989,7 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
             out->d_A_in[2 * i + 1] = b->sqk_h[i] * pb[2 * i + 1];
         }
     }
+    out->stored = stored ? 1 : 0;
     b->tau += h * (double)nsteps;
     {
         std::vector<int> sw(b->count);

@@ -449,6 +449,7 @@ def test_stored_and_recomputed_schedules_agree(prec, integ):
                           integrator=integ, **kw)
             b.set_grad_memory(budget)
             out[budget] = b.grad(5e-4, 37, T, segment=5)
+            assert b.last_grad_schedule == ("stored" if budget else "checkpoint")
             fin = b.get_state()
             b.close()
             out[budget]["final"] = fin
