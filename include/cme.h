@@ -73,7 +73,11 @@ typedef struct cme_options {
     int use_graph;         /* 1 = cme_step replays a cached CUDA graph per (h, nsteps) */
     int persistent;        /* batches with several N: 0 = library choice (1), 1 = one kernel
                               per N group (concurrent streams), 2 = one persistent work-list
-                              kernel for all groups */
+                              kernel for all groups.  FP32 groups of N > 4096 (8 values per
+                              thread, N = 2^15 ... 2^18): 2 runs every step of a call in one
+                              kernel whose blocks meet at grid-wide barriers (cooperative
+                              launch, where all its blocks fit on the GPU at once; otherwise,
+                              and with 0 or 1, two kernels per RK stage) */
     int cluster;           /* thread blocks per instance (1, 2, 4 or 8) for N = 2048 and 4096
                               at 8 values per thread: C > 1 spreads each instance over a
                               thread-block cluster that runs a four-step transform (an
@@ -216,13 +220,15 @@ int cme_get_time(cme_batch b, double* tau);
 int cme_set_time(cme_batch b, double tau);
 
 /* Per-instance status words (host array of `count` ints): 0 = finite, 1 = non-finite value
- * seen at the end of a launch, 2 = a bounded wait of a cluster all-to-all gave up (the
- * instance's results are not valid).  Synchronises. */
+ * seen at the end of a launch, 2 = a bounded wait of a cluster all-to-all or of a grid
+ * barrier (persistent = 2 for N > 4096) gave up (the instance's results are not valid).
+ * Synchronises. */
 int cme_status(cme_batch b, int* per_instance);
 
 /* Test of the failure path of the bounded device waits (not for normal use): what = 1 makes
  * the cluster all-to-alls of later cme_step / cme_grad calls expect 8 bytes more than are
- * sent and poll only briefly, so their waits run out; the instances then report status 2 and
+ * sent, and the grid barriers of the N > 4096 grid kernel one arrival more than there are
+ * blocks, and both poll only briefly, so their waits run out; the instances then report status 2 and
  * cme_synchronize / cme_grad return CME_ERR_TIMEOUT, with no device fault.  what = 0 restores
  * normal operation (cme_set_state clears the status words).  Batches without use_graph only.
  * Errors: INVALID_ARG. */

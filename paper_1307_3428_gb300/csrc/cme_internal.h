@@ -233,4 +233,11 @@ cudaError_t launch_large_col_fp32(int logN1, int R, const LargeArgs& a, long lon
 cudaError_t launch_large_col_fp64(int logN1, int R, const LargeArgs& a, long long cols,
                                   cudaStream_t s,
                                   bool pdl);
+// The grid-barrier kernel of FP32 four-step groups at 8 values per thread (cme_large.cuh:
+// large_grid_kernel), compiled for (log2 N1, log2 N2) in {(8, 7), (8, 8), (9, 8), (9, 9)}.
+// large_grid_fits: whether `blocks` blocks are resident at once on `sms` SMs (the condition of
+// its cooperative launch); launch_large_grid_fp32 launches a.nsteps steps as one kernel.
+bool large_grid_fits(int logN1, int logN2, long long blocks, int sms);
+cudaError_t launch_large_grid_fp32(int logN1, int logN2, const LargeArgs& a, long long blocks,
+                                   cudaStream_t s);
 }  // namespace cme

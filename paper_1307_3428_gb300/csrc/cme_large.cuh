@@ -55,6 +55,10 @@ struct LargeArgs {
     int stage;               // col kernel: LARGE_START, 0..3, LARGE_FINAL
     int diag;                // LDIAG_*: write to diag_out instead of continuing
     void* diag_out;          // [ninst][N] transform order (rhs) or time order (idft)
+    // grid-barrier kernel only
+    long long nsteps;        // steps of the launch
+    unsigned long long* bar; // arrival counter of the grid barriers, zero at launch
+    int bar_fault;           // test of the bounded waits: every barrier expects one arrival more
 };
 
 // Programmatic dependent launch: the step's kernels are launched so that each may start while
@@ -293,6 +297,254 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
         for (int j = 0; j < R; ++j)
             y[(long long)j * P * N2] = cmul(x[j], w[j]);   // * exp(+2 pi i j1 m2 / N)
     }
+}
+
+// ----------------------------------------------------------------------------------------
+// One launch for a whole call: the row and column passes of every stage of every step run in
+// one kernel whose blocks meet at grid-wide barriers instead of kernel boundaries.  Block b
+// owns column m2 = b mod N2 of instance b / N2 for the whole launch, so that column's field
+// (hi and compensation word) and Runge-Kutta accumulator stay in registers across steps, and
+// its output twiddles with them; in the row passes the same block takes rows b G .. b G + G - 1
+// (G = N1 / N2 rows of N2 / R threads: every block has N1 / R threads in both passes).  Only the
+// inter-pass buffers Y and Z go through memory, read past L1 (ld.global.cg: other SMs wrote
+// them since the last barrier).  Every block must be resident at once: the host launches it
+// cooperatively, on request (persistent = 2) and only where the occupancy allows it.  The
+// arithmetic is that of the row and column kernels above, expression for expression, so both
+// paths give the same bits.  On N = 2^17 it takes 35.4 us per step against 34.8 for the kernel
+// sequence: a block spends its time at the barriers waiting for the slowest block and, in the
+// fence before its arrival, for its strided stores (ncu: barrier, long-scoreboard and membar
+// stalls first), as the kernels of the sequence wait for them at exit.
+//
+// Barrier: the block's threads synchronise; thread 0 issues a GPU-scope fence (cumulative over
+// the block's writes ordered before it by the block barrier), adds one arrival to a 64-bit
+// counter, polls it until it reaches k x (blocks) for the k-th barrier of the launch, and
+// fences again before the block barrier that releases the other threads.  The poll is bounded: a block that gives up
+// reports status 2 for its column's instance and returns, and the others then give up at
+// their next barrier, so every wait ends.
+// ----------------------------------------------------------------------------------------
+CME_DEV unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+CME_DEV bool grid_barrier(unsigned long long* ctr, unsigned long long target, int tries, int* ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // release: the fence orders the block's earlier writes (through the block barrier)
+        // before the arrival, which is a reduction without a returned value
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
+        bool done = false;
+        for (int k = 0; k < tries && !done; ++k)
+            done = ld_relaxed_u64(ctr) >= target;
+        // acquire: later reads of the block (through the block barrier) after the observation
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        *ok = done;
+    }
+    __syncthreads();
+    return *ok != 0;
+}
+
+template <typename T>
+CME_DEV cx<T> ldcg(const cx<T>* p)
+{
+    const typename v2<T>::type v = __ldcg(reinterpret_cast<const typename v2<T>::type*>(p));
+    return {v.x, v.y};
+}
+
+template <typename T, int LOGN1, int LOGN2, int R>
+constexpr size_t large_grid_smem()
+{
+    return group_smem_bytes(sizeof(T), LOGN1, R) +
+           (size_t)(Plan<LOGN1, R>::P / Plan<LOGN2, R>::P) * group_smem_bytes(sizeof(T), LOGN2, R);
+}
+
+template <typename T, int LOGN1, int LOGN2, int R>
+__global__ void __launch_bounds__(Plan<LOGN1, R>::P) large_grid_kernel(const LargeArgs A)
+{
+    using GC = Group<T, LOGN1, R>;
+    using GW = Group<T, LOGN2, R>;
+    constexpr int N1 = GC::N, PC = GC::P, N2 = GW::N, PR = GW::P, GR = PC / PR;
+    static_assert(GR * PR == PC && (GR == 1 || GR == 2), "N1 = N2 or 2 N2");
+    constexpr long long N = (long long)N1 * N2;
+    constexpr bool COMP = GC::COMP;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int bar_ok;
+    const int tid = threadIdx.x;
+    // column pass: column m2 of instance ci
+    const int ci = (int)(blockIdx.x / N2);
+    const int m2 = (int)(blockIdx.x - (unsigned)ci * N2);
+    // row pass: row blockIdx.x G + g of the instance-major row list
+    const int g = tid / PR;
+    const long long row = (long long)blockIdx.x * GR + g;
+    const int ri = (int)(row / N1);
+    const int j1 = (int)(row - (long long)ri * N1);
+    GC gc;
+    gc.setup(smem, 0, tid, A.tw1);
+    GW gw;
+    gw.setup(smem + group_smem_bytes(sizeof(T), LOGN1, R), g, tid - g * PR, A.tw2);
+    const int t = gc.t, tr = gw.t;
+
+    const long long ibase = (long long)ci * N;
+    const long long e0 = ibase + (long long)m2 * N1 + t;   // column element j at e0 + j PC
+    const long long f0 = A.base + e0;
+    cx<T>* hi = reinterpret_cast<cx<T>*>(A.hi) + f0;
+    cx<T>* lo = reinterpret_cast<cx<T>*>(A.lo) + f0;
+    const cx<T>* Ep = reinterpret_cast<const cx<T>*>(A.E) + f0;
+    const cx<T>* e1p = reinterpret_cast<const cx<T>*>(A.e1) + f0;
+    const cx<T>* e2p = reinterpret_cast<const cx<T>*>(A.e2) + f0;
+    cx<T> Dh[R], Dl[R], Sv[R], wc[R], wr[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        Dh[j] = hi[j * PC];
+        Dl[j] = COMP ? lo[j * PC] : cx<T>{T(0), T(0)};
+        Sv[j] = cx<T>{T(0), T(0)};
+        wc[j] = gload<T>(A.twN, ((long long)(t + j * PC) * m2) & (N - 1));
+        wr[j] = gload<T>(A.twN, ((long long)j1 * (tr + j * PR)) & (N - 1));
+    }
+    const T gNr = (T)A.g0[ri] * ((T)1 / (T)N);
+    T h, hh, h6;
+    if constexpr (sizeof(T) == 4) {
+        h = A.hf;
+        hh = A.hhf;
+        h6 = A.h6f;
+    } else {
+        h = A.h;
+        hh = 0.5 * A.h;
+        h6 = A.h / 6.0;
+    }
+    cx<T>* ycol = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)t * N2 + m2;
+    const cx<T>* yrow = reinterpret_cast<const cx<T>*>(A.Y) + (long long)ri * N +
+                        (long long)j1 * N2 + tr;
+    cx<T>* zrow = reinterpret_cast<cx<T>*>(A.Z) + (long long)ri * N + (long long)tr * N1 + j1;
+    const cx<T>* zcol = reinterpret_cast<const cx<T>*>(A.Z) + e0;
+
+    const unsigned long long nb = gridDim.x;
+    const int tries = A.bar_fault ? 1024 : (1 << 22);
+    unsigned long long nbar = 0;
+    auto barrier = [&]() {
+        ++nbar;
+        return grid_barrier(A.bar, nbar * nb + (A.bar_fault ? 1 : 0), tries, &bar_ok);
+    };
+    // the inverse transform over m1 of a stage input, twiddle, store Y column m2
+    auto col_out = [&](cx<T>(&x)[R]) {
+        gc.inverse(x, 0);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            ycol[(long long)j * PC * N2] = cmul(x[j], wc[j]);   // * exp(+2 pi i j1 m2 / N)
+    };
+
+    bool ok;
+    {
+        cx<T> x[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            x[j] = Dh[j];
+        col_out(x);
+        ok = barrier();
+    }
+    for (long long s = 0; s < A.nsteps && ok; ++s) {
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+            // row pass: inverse over m2, Kerr term, forward over j2, twiddle, store Z
+            {
+                cx<T> x[R];
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    x[j] = ldcg(yrow + j * PR);
+                gw.rhs(x, gNr, cx<T>{T(0), T(0)});
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    zrow[(long long)j * PR * N1] = cmulc(x[j], wr[j]);   // * exp(-2 pi i j1 m2/N)
+            }
+            if (!(ok = barrier()))
+                break;
+            // column pass: forward over j1, Kerr factors, padding mask, pump
+            cx<T> x[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cx<T> v = ldcg(zcol + j * PC);
+                x[j] = {v.re, -v.im};
+            }
+            gc.inverse(x, 1);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                x[j].im = -x[j].im;
+            if (A.kerr) {
+                const T* km = reinterpret_cast<const T*>(A.kerr) + f0;
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    x[j] = cscale(x[j], __ldg(km + j * PC));
+            }
+            if (A.phys) {
+                const int M = A.phys[ci];
+                if (M < N) {
+                    const long long mlo = -(M / 2), mhi = M - M / 2 - 1;
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        const long long m = (long long)(t + j * PC) * N2 + m2;
+                        const long long mu = m >= N / 2 ? m - N : m;
+                        if (mu < mlo || mu > mhi)
+                            x[j] = cx<T>{T(0), T(0)};
+                    }
+                }
+            }
+            if (t == 0 && m2 == 0) {
+                const double2 pd = A.pump[ci];
+                x[0] = cadd(x[0], cx<T>{(T)pd.x, (T)pd.y});
+            }
+            // Runge-Kutta combination of stage st and the next stage's input
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cx<T> D = Dh[j];
+                if (st == 0) {
+                    const cx<T> Ev = gload<T>(Ep, j * PC), ev = gload<T>(e1p, j * PC);
+                    const cx<T> k1 = cmul(Ev, x[j]);
+                    Sv[j] = cmul(Ev, k1);
+                    x[j] = cadd(D, caxpy(cmul(ev, D), hh, k1));
+                } else if (st == 1) {
+                    const cx<T> Ev = gload<T>(Ep, j * PC), ev = gload<T>(e1p, j * PC);
+                    Sv[j] = caxpy(Sv[j], T(2), cmul(Ev, x[j]));
+                    x[j] = cadd(D, caxpy(cmul(ev, D), hh, x[j]));
+                } else if (st == 2) {
+                    const cx<T> Ev = gload<T>(Ep, j * PC), ev = gload<T>(e2p, j * PC);
+                    const cx<T> Ek3 = cmul(Ev, x[j]);
+                    Sv[j] = caxpy(Sv[j], T(2), Ek3);
+                    x[j] = cadd(D, caxpy(cmul(ev, D), h, Ek3));
+                } else {
+                    const cx<T> e2 = gload<T>(e2p, j * PC);
+                    cx<T> L = Dl[j];
+                    cx<T> Dn = D;
+                    cx<T> d = cmul(e2, D);
+                    if constexpr (COMP)
+                        d = cadd(d, cmul(e2, L));
+                    d = caxpy(d, h6, cadd(Sv[j], x[j]));
+                    accumulate<T, COMP>(Dn, L, d);
+                    Dh[j] = Dn;
+                    Dl[j] = L;
+                    if (!(isfinite(Dn.re) && isfinite(Dn.im)))
+                        A.status[ci] = 1;
+                    x[j] = Dn;
+                }
+            }
+            if (st == 3 && s == A.nsteps - 1)
+                break;   // the last step's field stays in registers until the store below
+            col_out(x);
+            if (!(ok = barrier()))
+                break;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        hi[j * PC] = Dh[j];
+        if constexpr (COMP)
+            lo[j * PC] = Dl[j];
+    }
+    if (!ok && tid == 0)
+        A.status[ci] = 2;
 }
 
 }  // namespace cme

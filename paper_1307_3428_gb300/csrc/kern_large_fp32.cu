@@ -45,4 +45,62 @@ cudaError_t launch_large_col_fp32(int logN1, int R, const LargeArgs& a, long lon
     }
 }
 
+#define CME_GRID_SHAPES(X) X(8, 7) X(8, 8) X(9, 8) X(9, 9)
+
+bool large_grid_fits(int logN1, int logN2, long long blocks, int sms)
+{
+    switch (logN1 * 32 + logN2) {
+#define CME_CASE(L1, L2)                                                                    \
+    case L1 * 32 + L2: {                                                                     \
+        auto k = large_grid_kernel<float, L1, L2, 8>;                                        \
+        constexpr size_t smem = large_grid_smem<float, L1, L2, 8>();                          \
+        if (prepare_smem(k, smem) != cudaSuccess) {                                          \
+            cudaGetLastError();                                                              \
+            return false;                                                                    \
+        }                                                                                    \
+        int per = 0;                                                                         \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, Plan<L1, 8>::P, smem) !=  \
+            cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                              \
+            return false;                                                                    \
+        }                                                                                    \
+        return (long long)per * sms >= blocks;                                               \
+    }
+        CME_GRID_SHAPES(CME_CASE)
+#undef CME_CASE
+    default:
+        return false;
+    }
+}
+
+cudaError_t launch_large_grid_fp32(int logN1, int logN2, const LargeArgs& a, long long blocks,
+                                   cudaStream_t s)
+{
+    switch (logN1 * 32 + logN2) {
+#define CME_CASE(L1, L2)                                                                    \
+    case L1 * 32 + L2: {                                                                     \
+        auto k = large_grid_kernel<float, L1, L2, 8>;                                        \
+        constexpr size_t smem = large_grid_smem<float, L1, L2, 8>();                          \
+        cudaError_t e = prepare_smem(k, smem);                                               \
+        if (e != cudaSuccess)                                                                \
+            return e;                                                                        \
+        cudaLaunchConfig_t cfg = {};                                                         \
+        cfg.gridDim = dim3((unsigned)blocks, 1, 1);                                          \
+        cfg.blockDim = dim3(Plan<L1, 8>::P, 1, 1);                                           \
+        cfg.dynamicSmemBytes = smem;                                                         \
+        cfg.stream = s;                                                                      \
+        cudaLaunchAttribute at[1];                                                           \
+        at[0].id = cudaLaunchAttributeCooperative;                                           \
+        at[0].val.cooperative = 1;                                                           \
+        cfg.attrs = at;                                                                      \
+        cfg.numAttrs = 1;                                                                    \
+        return cudaLaunchKernelEx(&cfg, k, a);                                               \
+    }
+        CME_GRID_SHAPES(CME_CASE)
+#undef CME_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace cme

@@ -137,3 +137,62 @@ def test_four_values_per_thread(N, prec):
     refs = fft_engine.rk4ip(fft_engine.Batch(insts), 1e-4, 40)
     for g, r in zip(got, refs):
         assert rel(g, r) <= (1e-12 if prec == cme.FP64 else 1e-5)
+
+
+# FP32 four-step groups whose column blocks all fit on the GPU at once: (N, instances)
+GRID_CASES = [(32768, 2), (65536, 2), (131072, 2), (262144, 1)]
+
+
+@pytest.mark.parametrize("N,count", GRID_CASES)
+def test_grid_kernel_matches_the_kernel_sequence_bitwise(N, count):
+    """With persistent = 2 such groups run every step of a call in one kernel whose blocks
+    meet at grid barriers (plan persistent 2, one launch per call); by default they run two
+    kernels per RK stage.  The grid kernel repeats the row and column kernels' arithmetic
+    expression for expression, so the two give the same bits: here with padding modes in one
+    instance and per-mode Kerr coefficients in another, over 25 steps."""
+    insts = [wl.make_instance(N, 1e-3, 1e-6, 2.0 + k, 2.0, 1e-4, seed=2600 + k)
+             for k in range(count)]
+    insts[0].M = (3 * N) // 4 + 1
+    if count > 1:
+        insts[1].g0_mu = wl.kerr_slope(1.0, N, 0.3)
+    grid = batch_of(insts, cme.FP32, persistent=2)
+    seq = batch_of(insts, cme.FP32)
+    assert grid.plan(0)["persistent"] == 2 and seq.plan(0)["persistent"] == 1
+    grid.step(2e-4, 25)
+    seq.step(2e-4, 25)
+    assert np.array_equal(grid.get_state(), seq.get_state())
+    assert list(grid.status()) == [0] * count
+    # a second call (propagators already computed for this h) is one launch, and continues
+    # from the stored state
+    grid.synchronize()
+    n0 = cme.kernel_launches()
+    grid.step(2e-4, 7)
+    grid.synchronize()
+    assert cme.kernel_launches() - n0 == 1
+    seq.step(2e-4, 7)
+    assert np.array_equal(grid.get_state(), seq.get_state())
+
+
+def test_grid_barrier_wait_is_bounded():
+    """Failure detection of the grid barriers without a device fault: the test switch
+    (cme_debug_fault) makes every barrier expect one arrival more than there are blocks, so
+    each block's poll runs out; the kernel finishes, the instance reports status 2,
+    cme_synchronize returns TIMEOUT, and the batch then steps correctly again."""
+    N = 32768
+    inst = wl.make_instance(N, 1e-3, 1e-6, 2.5, 2.0, 1e-4, seed=2650)
+    b = batch_of([inst], cme.FP32, persistent=2)
+    assert b.plan(0)["persistent"] == 2
+    D0 = b.get_state()
+    b.debug_fault(1)
+    b.step(2e-4, 3)
+    with pytest.raises(cme.CmeError) as e:
+        b.synchronize()
+    assert e.value.code == -5
+    assert list(b.status()) == [2]
+    b.debug_fault(0)
+    b.set_state(D0)
+    b.step(2e-4, 10)
+    b.synchronize()
+    assert list(b.status()) == [0]
+    ref = fft_engine.rk4ip(fft_engine.Batch([inst]), 2e-4, 10)[0]
+    assert rel(b.get_state(), ref) <= 1e-5
