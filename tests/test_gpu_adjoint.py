@@ -88,7 +88,7 @@ def test_grad_matches_central_differences_fp64():
               ("Are", 2e-6, lambda s: loss(A_in=inst.A_in + s), g["d_A_in"][0].real),
               ("Aim", 2e-6, lambda s: loss(A_in=inst.A_in + 1j * s), g["d_A_in"][0].imag)]
     rng = np.random.default_rng(62)
-    for r in range(3):
+    for r in range(8):
         v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
         v *= 1e-3 / np.linalg.norm(v)          # direction of the size of the noise floor
         checks.append((f"D0_{r}", 1e-6, lambda s, v=v: loss(D0=inst.D0 + s * v),
@@ -128,7 +128,7 @@ def test_grad_adjoint4096_full_horizon_matches_central_differences():
     FP64 loss, within 1e-6 relative plus the rounding noise of the difference quotient
     (fd_tolerance); the perturbed runs are independent instances of one batch.
 
-    Steps (reading 12a): sigma, |A_in| and every initial-field mode (three seeded directions
+    Steps (reading 12a): sigma, |A_in| and every initial-field mode (eight seeded directions
     v = D0 * w, w complex Gaussian) enter smoothly and take 1e-5 relative; 1e-6 leaves the
     quotient at the loss's rounding noise where a derivative is small against L / parameter
     (instance 7's dL/dRe A_in = 3.7 beside L = 5e5: 5.6e-6 off at 1e-6, measured).  D2 and D3
@@ -166,7 +166,7 @@ def test_grad_adjoint4096_full_horizon_matches_central_differences():
             ("D3", k, 1e-7 * 1e-4, lambda i, s: setattr(i, "omega", i.omega + s * mu ** 3 / 6),
              g["d_D3"][k]),
         ]
-        for r in range(3):
+        for r in range(8):
             v = inst.D0 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
             dirs.append((f"D0 direction {r}", k, 1e-5,
                          lambda i, s, v=v: setattr(i, "D0", i.D0 + s * v),
@@ -335,7 +335,7 @@ def test_strang_grad_matches_central_differences_fp64():
     """N = 4096 on 8-block clusters and N = 256 on one block, 400 Strang steps of the sweep-like
     dynamics: fourth-order central differences of the GPU FP64 loss agree with the adjoint to
     1e-6 relative plus the difference quotient's rounding noise (fd_tolerance).  Steps 1e-5
-    relative to sigma, |A_in| and each initial-field mode (three seeded directions), 1e-6
+    relative to sigma, |A_in| and each initial-field mode (eight seeded directions), 1e-6
     relative to D2 and to D3 (1e-7 at N = 4096; see the N = 4096 RK4IP check).  dL/dsigma of
     the N = 4096 run is small (1e-8 of L / sigma), so it is resolved only to the noise."""
     for N, h, n in ((256, 2e-3, 400), (4096, 2e-4, 400)):
@@ -357,7 +357,7 @@ def test_strang_grad_matches_central_differences_fp64():
                  g["d_D2"][0]),
                 ("D3", e_D3 * 1e-4, lambda i, s: setattr(i, "omega", i.omega + s * mu ** 3 / 6),
                  g["d_D3"][0])]
-        for r in range(3):
+        for r in range(8):
             v = inst.D0 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
             dirs.append((f"D0 direction {r}", 1e-5, lambda i, s, v=v: setattr(i, "D0", i.D0 + s * v),
                          float(np.real(np.vdot(g["d_D0"], v)))))
