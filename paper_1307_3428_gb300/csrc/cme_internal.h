@@ -36,6 +36,7 @@ struct StepArgs {
     void* diag_out;         // diagnostics output (same layout as the field)
     int a2a_fault;          // test of the bounded waits: cluster all-to-alls expect 8 bytes
                             // more than are sent and poll briefly (0 in normal use)
+    int smem_min;           // one-block launches: at least this much dynamic shared memory
 };
 
 // Shared-memory footprint of one instance group (one instance of N = 2^logN handled by N/R

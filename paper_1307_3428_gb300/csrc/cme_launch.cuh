@@ -1,6 +1,8 @@
 // Launch helpers shared by the per-precision kernel translation units.
 #pragma once
 
+#include <algorithm>
+
 #include "cme_step.cuh"
 
 namespace cme {
@@ -100,7 +102,7 @@ inline cudaError_t launch_step_shape(const StepArgs& a, cudaStream_t s)
     constexpr int P = Plan<LOGN, R>::P;
     const int threads = P * a.G;
     const int blocks = (a.ninst + a.G - 1) / a.G;
-    const size_t smem = smem_bytes_for<T>(LOGN, R, a.G);
+    const size_t smem = std::max(smem_bytes_for<T>(LOGN, R, a.G), (size_t)a.smem_min);
     auto k = step_kernel<T, LOGN, R, METHOD, MASKABLE>;
     cudaError_t e = prepare_smem(k, smem);
     if (e != cudaSuccess)
