@@ -75,6 +75,18 @@ __global__ void prop_kernel(PropArgs a)
             c = make_double2(qr * p.x - qi * p.y, qr * p.y + qi * p.x);
         }
         a.cpump[i] = c;
+        if (a.cpump2) {
+            // over h: (exp(L_0 h) - 1) / L_0 * pump   (h * pump when L_0 = 0)
+            double2 c2;
+            if (den == 0.0) {
+                c2 = make_double2(a.h * p.x, a.h * p.y);
+            } else {
+                const double qr = (e2.x * Lr + e2.y * Li) / den;
+                const double qi = (e2.y * Lr - e2.x * Li) / den;
+                c2 = make_double2(qr * p.x - qi * p.y, qr * p.y + qi * p.x);
+            }
+            a.cpump2[i] = c2;
+        }
         if (a.cphi) {
             // phi(L) = (exp(L hh) - 1)/L and phi'(L) = (hh exp(L hh) - phi(L))/L; for small
             // |z| = |L hh| the series phi'(L) = hh^2 sum_{k>=1} k z^(k-1)/(k+1)! (12 terms,

@@ -185,7 +185,7 @@ struct cme_batch_s {
     void *hi = nullptr, *lo = nullptr, *E = nullptr, *e1 = nullptr, *e2 = nullptr,
          *diag = nullptr;
     double *kappa = nullptr, *omega = nullptr, *sigma_d = nullptr, *g0_d = nullptr;
-    double2 *pump_d = nullptr, *cpump_d = nullptr, *stage = nullptr;
+    double2 *pump_d = nullptr, *cpump_d = nullptr, *cpump2_d = nullptr, *stage = nullptr;
     double2* cphi_d = nullptr;   // per instance phi(L_0), phi'(L_0) of the Strang pump increment
     int *mode_inst = nullptr, *inst_N = nullptr, *status_d = nullptr;
     int* phys_d = nullptr;   // per-instance physical mode count M
@@ -699,6 +699,7 @@ int cme_batch_create(const cme_instance* v, int count, const cme_options* opt, v
     b->g0_d = (double*)A(count * 8);
     b->pump_d = (double2*)A(count * 16);
     b->cpump_d = (double2*)A(count * 16);
+    b->cpump2_d = (double2*)A(count * 16);
     b->cphi_d = (double2*)A(count * 32);
     b->inst_N = (int*)A(count * 4);
     b->status_d = (int*)A(count * 4);
@@ -917,6 +918,7 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
     a.tw = b->tw[g.logN];
     a.pump = b->pump_d + g.first;
     a.cpump = b->cpump_d + g.first;
+    a.cpump2 = b->cpump2_d + g.first;
     a.g0 = b->g0_d + g.first;
     a.status = b->status_d + g.first;
     a.phys = g.masked ? b->phys_d + g.first : nullptr;   // null: no padding modes in the group
@@ -1198,6 +1200,7 @@ int ensure_propagators(cme_batch b, double h)
     p.e1 = b->e1;
     p.e2 = b->e2;
     p.cpump = b->cpump_d;
+    p.cpump2 = b->cpump2_d;
     p.ninst = b->count;
     p.cphi = b->cphi_d;
     ++g_launches;

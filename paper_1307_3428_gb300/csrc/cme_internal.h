@@ -24,6 +24,7 @@ struct StepArgs {
     const void* tw;         // twiddle table exp(2 pi i k / N), k < N
     const double2* pump;    // per-instance pump sqrt(kappa_ext) A_in (group-relative)
     const double2* cpump;   // per-instance Strang pump increment over h/2
+    const double2* cpump2;  // ... over h (merged linear flows between Strang steps), or null
     const double* g0;       // per-instance Kerr coefficient g0
     int* status;            // per-instance status (group-relative)
     const int* phys;        // per-instance physical mode count M (group-relative; null: all N)
@@ -127,6 +128,7 @@ struct PropArgs {
     void* e2;
     void* e1h;                // Strang: expm1(L h/2)
     double2* cpump;           // Strang pump increment per instance
+    double2* cpump2;          // the same over h (null: not computed)
     int ninst;
     double2* cphi;            // optional (null: skipped): per instance phi(L_0) and phi'(L_0),
                               // phi(L) = (exp(L h/2) - 1)/L, the factor of the Strang pump

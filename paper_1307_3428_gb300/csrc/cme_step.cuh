@@ -497,6 +497,7 @@ template <typename T>
 struct StepConsts {
     cx<T> pump;   // sqrt(kappa_ext) A_in
     cx<T> cp;     // Strang pump increment over h/2
+    cx<T> cp2;    // ... over h
     T gN;         // g0 / N
     T g0h;        // g0 h / 2 (Strang half phase per |a|^2)
     T h, hh, h6;
@@ -592,85 +593,108 @@ CME_DEV void small_sincos(float y, float& s, float& c)
     }
 }
 
+// Linear and pump flow of the Strang step, exact, applied as the increment D += e D + c: over
+// h/2 (full = false: e = expm1(L h/2), c = (exp(L_0 h/2) - 1)/L_0 sqrt(kappa_ext) A_in on the
+// pumped mode) or over h (full = true: e = expm1(L h), c the same over h).
+template <typename T, int LOGN, int R, int C>
+CME_DEV void strang_linear(const Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                           const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c, bool full)
+{
+    constexpr bool COMP = Group<T, LOGN, R, C>::COMP;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const cx<T> e = full ? pr.get2(j) : pr.get1(j);
+        cx<T> d = cmul(e, fs.Dh[j]);
+        if constexpr (COMP)
+            d = cadd(d, cmul(e, fs.getL(j)));
+        if (j == 0 && grp.t == 0)
+            d = cadd(d, full ? c.cp2 : c.cp);
+        fs.add(j, d);
+    }
+}
+
+// Exact Kerr flow of the Strang step over h.  With a = inverse transform of D the flow is
+// a -> a exp(i g0 |a|^2 h); it is applied as the increment D += DFT(a expm1(i g0 |a|^2 h))/N.
+// STORE = true also stores, unless so is null (the adjoint's recomputation), the time-domain
+// field a at so[j P] and the state after the flow at so[sstride + j P].
+template <bool STORE, typename T, int LOGN, int R, int C>
+CME_DEV void strang_kerr(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                         const StepConsts<T>& c, cx<T>* so, long long sstride)
+{
+    constexpr int P = Group<T, LOGN, R, C>::P;
+    constexpr T invN = (T)(1.0 / (1 << LOGN));
+    cx<T> x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        x[j] = fs.Dh[j];
+#pragma unroll 1
+    for (int d = 0; d < 2; ++d) {
+        grp.inverse(x, d);
+        if constexpr (STORE) {
+            if (d == 0 && so) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    so[j * P] = x[j];
+            }
+        }
+        if (d == 0) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h; the forward
+                // transform runs as conj(inverse(conj(.)))
+                const T ph2 = c.g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
+                T s, co;
+                if constexpr (sizeof(T) == 4)
+                    small_sincos(ph2, s, co);
+                else
+                    sincos(ph2, &s, &co);
+                const cx<T> em = {T(-2) * s * s * invN, T(2) * s * co * invN};
+                const cx<T> b = cmul(x[j], em);
+                x[j] = {b.re, -b.im};
+            }
+        }
+    }
+    grp.mask(x);   // no Kerr increment on padding modes
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        fs.add(j, cx<T>{x[j].re, -x[j].im});
+    if constexpr (STORE) {
+        if (so) {
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                so[sstride + j * P] = fs.Dh[j];
+        }
+    }
+}
+
 // One Strang split step (Sec. 2 "split-step Fourier method ... field in the frequency domain"):
 // exact linear+pump flow over h/2, exact Kerr flow over h, exact linear+pump flow over h/2.
-// With a = inverse transform of D the Kerr flow is a -> a exp(i g0 |a|^2 h); it is applied as
-// the increment D += DFT(a expm1(i g0 |a|^2 h))/N.
-// STORE = true also stores, unless so is null (the adjoint's recomputation), the time-domain
-// field a of the Kerr flow at so[j P] and the state after the Kerr flow at so[sstride + j P].
+// The adjoint's recomputation takes the steps one by one (STORE: see strang_kerr).
 template <bool STORE, typename T, int LOGN, int R, int C>
 CME_DEV void strang_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
                               const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c, cx<T>* so,
                               long long sstride)
 {
-    constexpr int P = Group<T, LOGN, R, C>::P;
-    constexpr bool COMP = Group<T, LOGN, R, C>::COMP;
-    constexpr T invN = (T)(1.0 / (1 << LOGN));
-#pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-        if (half == 1) {
-            cx<T> x[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                x[j] = fs.Dh[j];
-#pragma unroll 1
-            for (int d = 0; d < 2; ++d) {
-                grp.inverse(x, d);
-                if constexpr (STORE) {
-                    if (d == 0 && so) {
-#pragma unroll
-                        for (int j = 0; j < R; ++j)
-                            so[j * P] = x[j];
-                    }
-                }
-                if (d == 0) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h; the
-                        // forward transform runs as conj(inverse(conj(.)))
-                        const T ph2 = c.g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
-                        T s, co;
-                        if constexpr (sizeof(T) == 4)
-                            small_sincos(ph2, s, co);
-                        else
-                            sincos(ph2, &s, &co);
-                        const cx<T> em = {T(-2) * s * s * invN, T(2) * s * co * invN};
-                        const cx<T> b = cmul(x[j], em);
-                        x[j] = {b.re, -b.im};
-                    }
-                }
-            }
-            grp.mask(x);   // no Kerr increment on padding modes
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                fs.add(j, cx<T>{x[j].re, -x[j].im});
-            if constexpr (STORE) {
-                if (so) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j)
-                        so[sstride + j * P] = fs.Dh[j];
-                }
-            }
-        }
-        // linear + pump half step: D += e1 D + delta_{mu,0} c
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const cx<T> e1 = pr.get1(j);
-            cx<T> d = cmul(e1, fs.Dh[j]);
-            if constexpr (COMP)
-                d = cadd(d, cmul(e1, fs.getL(j)));
-            if (j == 0 && grp.t == 0)
-                d = cadd(d, c.cp);
-            fs.add(j, d);
-        }
-    }
+    strang_linear(grp, fs, pr, c, false);
+    strang_kerr<STORE>(grp, fs, c, so, sstride);
+    strang_linear(grp, fs, pr, c, false);
 }
 
+// n Strang steps as the step kernels take them: the half flow that closes a step and the half
+// flow that opens the next compose exactly into the flow over h (exp(L h/2)^2 = exp(L h), and
+// the pump increments into the increment over h), so the n steps apply n + 1 linear flows
+// instead of 2n.  The field after the n steps is that of n single steps up to rounding.
 template <typename T, int LOGN, int R, int C>
-CME_DEV void strang_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
-                         const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c)
+CME_DEV void strang_steps(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
+                          const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c, long long n)
 {
-    strang_step_impl<false>(grp, fs, pr, c, static_cast<cx<T>*>(nullptr), 0);
+    if (n <= 0)
+        return;
+    strang_linear(grp, fs, pr, c, false);
+    for (long long k = 0; k < n; ++k) {
+        strang_kerr<false>(grp, fs, c, static_cast<cx<T>*>(nullptr), 0);
+        strang_linear(grp, fs, pr, c, k + 1 < n);
+    }
 }
 
 template <typename T>
@@ -681,6 +705,8 @@ CME_DEV StepConsts<T> step_consts(const StepArgs& a, int inst, int N)
     c.pump = {(T)pd.x, (T)pd.y};
     const double2 cpd = a.cpump[inst];
     c.cp = {(T)cpd.x, (T)cpd.y};
+    const double2 cpd2 = a.cpump2 ? a.cpump2[inst] : make_double2(0.0, 0.0);
+    c.cp2 = {(T)cpd2.x, (T)cpd2.y};
     c.gN = (T)(a.g0[inst] / (double)N);
     c.g0h = (T)(a.g0[inst] * a.h * 0.5);
     c.h = Coef<T>::h(a);
@@ -723,11 +749,11 @@ CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
     Props<T, LOGN, R> pr;
     pr.init(a, off, t);
 
-    for (long long n = 0; n < a.nsteps; ++n) {
-        if constexpr (METHOD == METHOD_RK4IP)
+    if constexpr (METHOD == METHOD_RK4IP) {
+        for (long long n = 0; n < a.nsteps; ++n)
             rk4ip_step(grp, fs, pr, c);
-        else
-            strang_step(grp, fs, pr, c);
+    } else {
+        strang_steps(grp, fs, pr, c, a.nsteps);
     }
 
     bool bad = false;
@@ -776,11 +802,11 @@ __global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(cons
     pr.init(a, off, t);
     cluster_sync();   // every block of the cluster runs before the first remote store
 
-    for (long long n = 0; n < a.nsteps; ++n) {
-        if constexpr (METHOD == METHOD_RK4IP)
+    if constexpr (METHOD == METHOD_RK4IP) {
+        for (long long n = 0; n < a.nsteps; ++n)
             rk4ip_step(grp, fs, pr, c);
-        else
-            strang_step(grp, fs, pr, c);
+    } else {
+        strang_steps(grp, fs, pr, c, a.nsteps);
     }
 
     bool bad = false;
