@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
         if (valid) {
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                o[j * P] = fs.Dh[j];
+                sstore(o + j * P, fs.Dh[j]);
         }
         if constexpr (METHOD == METHOD_RK4IP)
             rk4ip_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);

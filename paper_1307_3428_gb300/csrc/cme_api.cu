@@ -933,12 +933,14 @@ StepArgs group_args(cme_batch b, const LaunchGroup& g)
 
 cudaError_t large_steps(cme_batch b, LaunchGroup& g, long long nsteps, cudaStream_t st);
 
-cudaError_t launch_group_step(cme_batch b, LaunchGroup& g, long long nsteps, cudaStream_t st)
+cudaError_t launch_group_step(cme_batch b, LaunchGroup& g, long long nsteps, cudaStream_t st,
+                              bool single_steps = false)
 {
     if (g.large)
         return large_steps(b, g, nsteps, st);
     StepArgs a = group_args(b, g);
     a.nsteps = nsteps;
+    a.single_steps = single_steps;
     // Concurrent groups: the groups whose blocks take over a third of an SM's shared memory
     // anyway launch with all of it, where their blocks fit one per SM together, so that each
     // such block has an SM to itself.  Where two N = 2048 blocks shared an SM, the uneven
@@ -1943,8 +1945,9 @@ extern "C" int cme_grad(cme_batch b, double h, long nsteps, const double* target
                                          cudaMemcpyDeviceToDevice, st),
                          "cme_grad: checkpoint");
             const long long n = std::min(K, (long long)nsteps - s * K);
+            // Strang steps one by one, as the recomputation reproduces them bit for bit
             for (auto& g : ag)
-                CME_CUDA(launch_group_step(b, g, n, st), "cme_grad: forward");
+                CME_CUDA(launch_group_step(b, g, n, st, true), "cme_grad: forward");
         }
     }
     // loss and its seed

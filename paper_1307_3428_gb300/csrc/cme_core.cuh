@@ -51,6 +51,17 @@ CME_DEV cx<T> gload(const void* p, long long i)
     const typename v2<T>::type v = __ldg(reinterpret_cast<const typename v2<T>::type*>(p) + i);
     return {v.x, v.y};
 }
+// Store of per-step scratch that is read back only much later (the adjoint's stored steps):
+// streaming (evict-first), so that it does not push the batch's tables out of L2.
+template <typename T>
+CME_DEV void sstore(cx<T>* p, cx<T> v)
+{
+    using V = typename v2<T>::type;
+    V w;
+    w.x = v.re;
+    w.y = v.im;
+    __stcs(reinterpret_cast<V*>(p), w);
+}
 template <typename T>
 CME_DEV cx<T> load(const void* p, long long i)
 {

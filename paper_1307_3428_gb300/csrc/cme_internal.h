@@ -38,6 +38,8 @@ struct StepArgs {
     int a2a_fault;          // test of the bounded waits: cluster all-to-alls expect 8 bytes
                             // more than are sent and poll briefly (0 in normal use)
     int smem_min;           // one-block launches: at least this much dynamic shared memory
+    int single_steps;       // Strang: every step on its own (no merged linear flows), as the
+                            // adjoint's recomputation takes them
 };
 
 // Shared-memory footprint of one instance group (one instance of N = 2^logN handled by N/R

@@ -265,7 +265,7 @@ struct Group {
             if (d == 0 && aout) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    aout[j * P] = x[j];
+                    sstore(aout + j * P, x[j]);
             }
             if (d == 0) {
                 // conj(i c a) with c = (g0/N) |a|^2
@@ -533,7 +533,7 @@ CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C
             if (st < 3 && so) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    so[st * sstride + j * P] = x[j];
+                    sstore(so + st * sstride + j * P, x[j]);
             }
         }
         if (st == 0) {
@@ -634,7 +634,7 @@ CME_DEV void strang_kerr(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
             if (d == 0 && so) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    so[j * P] = x[j];
+                    sstore(so + j * P, x[j]);
             }
         }
         if (d == 0) {
@@ -662,7 +662,7 @@ CME_DEV void strang_kerr(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
         if (so) {
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                so[sstride + j * P] = fs.Dh[j];
+                sstore(so + sstride + j * P, fs.Dh[j]);
         }
     }
 }
@@ -753,7 +753,9 @@ CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
         for (long long n = 0; n < a.nsteps; ++n)
             rk4ip_step(grp, fs, pr, c);
     } else {
-        strang_steps(grp, fs, pr, c, a.nsteps);
+        const long long m = a.single_steps ? 1 : a.nsteps;
+        for (long long n = 0; n < a.nsteps; n += m)
+            strang_steps(grp, fs, pr, c, a.nsteps - n < m ? a.nsteps - n : m);
     }
 
     bool bad = false;
@@ -806,7 +808,9 @@ __global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(cons
         for (long long n = 0; n < a.nsteps; ++n)
             rk4ip_step(grp, fs, pr, c);
     } else {
-        strang_steps(grp, fs, pr, c, a.nsteps);
+        const long long m = a.single_steps ? 1 : a.nsteps;
+        for (long long n = 0; n < a.nsteps; n += m)
+            strang_steps(grp, fs, pr, c, a.nsteps - n < m ? a.nsteps - n : m);
     }
 
     bool bad = false;
