@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) segment_kernel(cons
                 sstore(o + j * P, fs.Dh[j]);
         }
         if constexpr (METHOD == METHOD_RK4IP)
-            rk4ip_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
+            rk4ip_step_impl<true, rk_cache_ed<T, LOGN, R, C>()>(grp, fs, pr, c,
+                                                               valid ? o + TT : nullptr, TT);
         else
             strang_step_impl<true>(grp, fs, pr, c, valid ? o + TT : nullptr, TT);
     }

@@ -15,7 +15,7 @@ template <typename T, int LOGN, int R, int METHOD>
 __device__ __noinline__ void fused_tile(const StepArgs* a, int first)
 {
     extern __shared__ __align__(16) unsigned char smem_tile[];
-    step_body<T, LOGN, R, METHOD>(*a, first, smem_tile);
+    step_body<T, LOGN, R, METHOD, true, true>(*a, first, smem_tile);
 }
 
 template <typename T, int METHOD>

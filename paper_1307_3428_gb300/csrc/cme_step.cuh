@@ -512,7 +512,7 @@ struct StepConsts {
 // values y1 = F(D), k2 = F(x2), k3 = F(x3) of the thread's positions at so[st * sstride + j P],
 // st = 0, 1, 2, and the time-domain fields a of the four stage inputs D, x2, x3, x4 at
 // so[(3 + st) * sstride + j P], st = 0..3.
-template <bool STAGES, typename T, int LOGN, int R, int C>
+template <bool STAGES, bool CACHE = false, typename T, int LOGN, int R, int C>
 CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
                              const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c, cx<T>* so,
                              long long sstride)
@@ -520,6 +520,9 @@ CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C
     constexpr bool COMP = Group<T, LOGN, R, C>::COMP;
     constexpr int P = Group<T, LOGN, R, C>::P;
     cx<T> x[R];
+    // CACHE: e1 D (stages 0, 1), then e2 D (stages 2, 3) computed once and kept in registers
+    // across the stage's transforms (kernels with registers to spare); else recomputed
+    cx<T> eD[CACHE ? R : 1];
 #pragma unroll
     for (int j = 0; j < R; ++j)
         x[j] = fs.Dh[j];
@@ -542,26 +545,41 @@ CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C
                 const cx<T> E = pr.getE(j);
                 const cx<T> k1 = cmul(E, x[j]);
                 fs.setS(j, cmul(E, k1));
-                x[j] = cadd(fs.Dh[j], caxpy(cmul(pr.get1(j), fs.Dh[j]), c.hh, k1));
+                const cx<T> e1D = cmul(pr.get1(j), fs.Dh[j]);
+                if constexpr (CACHE)
+                    eD[j] = e1D;
+                x[j] = cadd(fs.Dh[j], caxpy(e1D, c.hh, k1));
             }
         } else if (st == 1) {
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 fs.setS(j, caxpy(fs.getS(j), T(2), cmul(pr.getE(j), x[j])));
-                x[j] = cadd(fs.Dh[j], caxpy(cmul(pr.get1(j), fs.Dh[j]), c.hh, x[j]));
+                cx<T> e1D;
+                if constexpr (CACHE)
+                    e1D = eD[j];
+                else
+                    e1D = cmul(pr.get1(j), fs.Dh[j]);
+                x[j] = cadd(fs.Dh[j], caxpy(e1D, c.hh, x[j]));
             }
         } else if (st == 2) {
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 const cx<T> Ek3 = cmul(pr.getE(j), x[j]);
                 fs.setS(j, caxpy(fs.getS(j), T(2), Ek3));
-                x[j] = cadd(fs.Dh[j], caxpy(cmul(pr.get2(j), fs.Dh[j]), c.h, Ek3));
+                const cx<T> e2D = cmul(pr.get2(j), fs.Dh[j]);
+                if constexpr (CACHE)
+                    eD[j] = e2D;
+                x[j] = cadd(fs.Dh[j], caxpy(e2D, c.h, Ek3));
             }
         } else {
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 const cx<T> e2 = pr.get2(j);
-                cx<T> d = cmul(e2, fs.Dh[j]);
+                cx<T> d;
+                if constexpr (CACHE)
+                    d = eD[j];
+                else
+                    d = cmul(e2, fs.Dh[j]);
                 if constexpr (COMP)
                     d = cadd(d, cmul(e2, fs.getL(j)));
                 d = caxpy(d, c.h6, cadd(fs.getS(j), x[j]));
@@ -571,11 +589,20 @@ CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C
     }
 }
 
+// Whether a step kernel has the registers to keep e1 D / e2 D across a stage (FP32 at 8 values
+// per thread, at most 256 threads per block: N = 512, 64 threads, 168 -> 192 registers), not
+// in the work-list kernel, whose tiles share one register budget.
 template <typename T, int LOGN, int R, int C>
+CME_HD constexpr bool rk_cache_ed()
+{
+    return sizeof(T) == 4 && R <= 8 && Plan<LOGN, R>::P / C <= 256;
+}
+
+template <bool CACHE = false, typename T, int LOGN, int R, int C>
 CME_DEV void rk4ip_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs,
                         const Props<T, LOGN, R, C>& pr, const StepConsts<T>& c)
 {
-    rk4ip_step_impl<false>(grp, fs, pr, c, static_cast<cx<T>*>(nullptr), 0);
+    rk4ip_step_impl<false, CACHE>(grp, fs, pr, c, static_cast<cx<T>*>(nullptr), 0);
 }
 
 // sin y and cos y in FP32 for the Strang Kerr phase y = g0 |a|^2 h / 2, which is small in any
@@ -719,7 +746,7 @@ CME_DEV StepConsts<T> step_consts(const StepArgs& a, int inst, int N)
 // (group-relative indices; groups past a.ninst recompute the last instance and store nothing).
 // MASKABLE = false compiles the body without the physical-mode mask (every instance M = N):
 // the mask test then folds away at compile time.
-template <typename T, int LOGN, int R, int METHOD, bool MASKABLE = true>
+template <typename T, int LOGN, int R, int METHOD, bool MASKABLE = true, bool FUSED = false>
 CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
 {
     using GR = Group<T, LOGN, R>;
@@ -751,7 +778,7 @@ CME_DEV void step_body(const StepArgs& a, int first, unsigned char* smem)
 
     if constexpr (METHOD == METHOD_RK4IP) {
         for (long long n = 0; n < a.nsteps; ++n)
-            rk4ip_step(grp, fs, pr, c);
+            rk4ip_step<!FUSED && rk_cache_ed<T, LOGN, R, 1>()>(grp, fs, pr, c);
     } else {
         const long long m = a.single_steps ? 1 : a.nsteps;
         for (long long n = 0; n < a.nsteps; n += m)
@@ -806,7 +833,7 @@ __global__ void __launch_bounds__(Plan<LOGN, R>::P / C) cluster_step_kernel(cons
 
     if constexpr (METHOD == METHOD_RK4IP) {
         for (long long n = 0; n < a.nsteps; ++n)
-            rk4ip_step(grp, fs, pr, c);
+            rk4ip_step<rk_cache_ed<T, LOGN, R, C>()>(grp, fs, pr, c);
     } else {
         const long long m = a.single_steps ? 1 : a.nsteps;
         for (long long n = 0; n < a.nsteps; n += m)
