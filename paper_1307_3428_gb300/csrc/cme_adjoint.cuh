@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
         Db[j] = dbp[j * P];
         gl[j].init(glp[j * P]);
     }
-    double2 pb = make_double2(0.0, 0.0);
-    if (t == 0)
-        pb = A.pbar[inst];
+    // the pump cotangent (thread 0 holds mode 0), accumulated like the L cotangents
+    LAcc<T> pb;
+    pb.init(t == 0 ? A.pbar[inst] : make_double2(0.0, 0.0));
     const T hh = c.hh, h = c.h, h6 = c.h6, h3 = T(2) * c.h6;
     const T gNn = c.gN;  // g0 / N
 
@@ -296,8 +296,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                 }
             }
             if (t == 0) {
-                pb.x += (double)cot[0].re;
-                pb.y += (double)cot[0].im;
+                pb.add(cot[0]);
             }
             // zbar = J_F(z)^H cot, a = IDFT(stage input) from the buffer: bbar =
             // IDFT(-i (g0/N) cot), then DFT(2 |a|^2 bbar + a^2 conj(bbar)) (two transforms
@@ -364,7 +363,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
             glp[j * P] = gl[j].finish(glp[j * P]);
         }
         if (t == 0)
-            A.pbar[inst] = pb;
+            A.pbar[inst] = pb.finish(A.pbar[inst]);
     }
     if ((grp.failed() || pf_failed) && a.status)
         a.status[inst] = 2;
@@ -416,9 +415,9 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) strang_adjoint_kern
         Db[j] = dbp[j * P];
         gl[j].init(glp[j * P]);
     }
-    double2 pb = make_double2(0.0, 0.0);
-    if (t == 0)
-        pb = A.pbar[inst];
+    // the pump cotangent (thread 0 holds mode 0), accumulated like the L cotangents
+    LAcc<T> pb;
+    pb.init(t == 0 ? A.pbar[inst] : make_double2(0.0, 0.0));
     const T hh = c.hh;
     const T gh = T(2) * c.g0h;                // g0 h
     constexpr T invN = (T)(1.0 / (1 << LOGN));
@@ -430,8 +429,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) strang_adjoint_kern
         const cx<T>* Dn = buf + i * ADJ_VECS * TT;
         // second linear half flow
         if (t == 0) {
-            pb.x += (double)Db[0].re;
-            pb.y += (double)Db[0].im;
+            pb.add(Db[0]);
         }
 #pragma unroll
         for (int j = 0; j < R; ++j) {
@@ -477,8 +475,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) strang_adjoint_kern
             Db[j] = cadd(Db[j], cconj(z[j]));                        // D1bar
         // first linear half flow
         if (t == 0) {
-            pb.x += (double)Db[0].re;
-            pb.y += (double)Db[0].im;
+            pb.add(Db[0]);
         }
 #pragma unroll
         for (int j = 0; j < R; ++j) {
@@ -494,7 +491,7 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) strang_adjoint_kern
             glp[j * P] = gl[j].finish(glp[j * P]);
         }
         if (t == 0)
-            A.pbar[inst] = pb;
+            A.pbar[inst] = pb.finish(A.pbar[inst]);
     }
     if (grp.failed() && a.status)
         a.status[inst] = 2;
