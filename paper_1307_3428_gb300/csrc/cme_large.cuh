@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
     }
 }
 
-// Column pass: instance i = col / N2, column m2 = col mod N2.
-template <typename T, int LOGN1, int R>
+// Column pass: instance i = col / N2, column m2 = col mod N2.  One instantiation per stage ST
+// (LARGE_START, 0 ... 3, LARGE_FINAL; A.stage is ST): each holds only its stage's code.
+template <typename T, int LOGN1, int R, int ST>
 __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(const LargeArgs A)
 {
     using GR = Group<T, LOGN1, R>;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     const cx<T>* Ep = reinterpret_cast<const cx<T>*>(A.E) + f0;
     const cx<T>* e1p = reinterpret_cast<const cx<T>*>(A.e1) + f0;
     const cx<T>* e2p = reinterpret_cast<const cx<T>*>(A.e2) + f0;
-    const int st = A.stage;
+    constexpr int st = ST;
     // Every operand of the Runge-Kutta combination and the output twiddles are loaded here,
     // before the transforms, so that their latency overlaps the first transform: the constant
     // ones (propagators, twiddles) even before the wait for the preceding kernel.
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     }
 
     cx<T> x[R];
-    if (A.stage != LARGE_START) {
+    if constexpr (ST != LARGE_START) {
         // forward transform over j1 of Z column m2, as conj(inverse(conj(.)))
         const cx<T>* z = reinterpret_cast<const cx<T>*>(A.Z) + e0;
 #pragma unroll

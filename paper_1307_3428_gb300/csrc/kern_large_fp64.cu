@@ -35,8 +35,29 @@ cudaError_t launch_large_col_fp64(int logN1, int R, const LargeArgs& a, long lon
     case LN * 32 + RR: {                                                                    \
         constexpr int P = Plan<LN, RR>::P;                                        \
         const size_t smem = smem_bytes_for<double>(LN, RR, a.G);                    \
-        auto k = large_col_kernel<double, LN, RR>;                                  \
-        return launch_pdl(k, (unsigned)((cols + a.G - 1) / a.G), P * a.G, smem, s, pdl, a); \
+        const unsigned blocks = (unsigned)((cols + a.G - 1) / a.G);                \
+        switch (a.stage) {                                                         \
+        case LARGE_START:                                                          \
+            return launch_pdl(large_col_kernel<double, LN, RR, LARGE_START>, blocks, P * a.G, \
+                              smem, s, pdl, a);                                    \
+        case 0:                                                                    \
+            return launch_pdl(large_col_kernel<double, LN, RR, 0>, blocks, P * a.G, smem, s, \
+                              pdl, a);                                             \
+        case 1:                                                                    \
+            return launch_pdl(large_col_kernel<double, LN, RR, 1>, blocks, P * a.G, smem, s, \
+                              pdl, a);                                             \
+        case 2:                                                                    \
+            return launch_pdl(large_col_kernel<double, LN, RR, 2>, blocks, P * a.G, smem, s, \
+                              pdl, a);                                             \
+        case 3:                                                                    \
+            return launch_pdl(large_col_kernel<double, LN, RR, 3>, blocks, P * a.G, smem, s, \
+                              pdl, a);                                             \
+        case LARGE_FINAL:                                                          \
+            return launch_pdl(large_col_kernel<double, LN, RR, LARGE_FINAL>, blocks, P * a.G, \
+                              smem, s, pdl, a);                                    \
+        default:                                                                   \
+            return cudaErrorInvalidValue;                                          \
+        }                                                                          \
     }
         CME_LARGE_SHAPES(CME_CASE)
 #undef CME_CASE
