@@ -526,8 +526,8 @@ CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C
 #pragma unroll
     for (int j = 0; j < R; ++j)
         x[j] = fs.Dh[j];
-#pragma unroll 1
-    for (int st = 0; st < 4; ++st) {
+    // one RK stage (st = 0 ... 3)
+    auto stage = [&](int st) {
         if constexpr (STAGES)
             grp.rhs_store_a(x, c.gN, c.pump, so ? so + (3 + st) * sstride : nullptr);
         else
@@ -586,6 +586,19 @@ CME_DEV void rk4ip_step_impl(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C
                 fs.add(j, d);
             }
         }
+    };
+    // One-block CACHE kernels (registers to spare) take the four stages unrolled: 51.6 -> 49.4
+    // ms per headline run.  Elsewhere one copy of the stage code in a loop keeps the
+    // instruction footprint small: unrolled, the 8-block cluster kernel of N = 4096 took 6.9
+    // instead of 5.1 us per step.
+    if constexpr (CACHE && C == 1) {
+#pragma unroll
+        for (int st = 0; st < 4; ++st)
+            stage(st);
+    } else {
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st)
+            stage(st);
     }
 }
 
