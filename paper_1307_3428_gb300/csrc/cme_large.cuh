@@ -18,8 +18,10 @@
 //        input, twiddle, store Y column m2.
 // The field, the accumulator S and the propagators stay in HBM (L2-resident at these sizes),
 // stored column-major (mode m1 N2 + m2 at position m2 N1 + m1) so that the column kernel reads
-// them contiguously; Y (row-major) and Z (column-major) are the inter-pass buffers (scratch),
-// laid out so that both kernels read contiguously and only their stores are strided.
+// them contiguously; Y (column-major) and Z (row-major) are the inter-pass buffers (scratch),
+// laid out so that both kernels store them contiguously and only read them strided: a kernel
+// waits at its exit for its stores, and strided stores made that wait the longest stall (N =
+// 2^17: 31.7 -> 29.6 us per step with the strides moved to the loads).
 #pragma once
 
 #include "cme_step.cuh"
@@ -37,8 +39,8 @@ struct LargeArgs {
     void* hi;                // field (FP32: hi part)
     void* lo;                // FP32 compensation word
     void* S;                 // Runge-Kutta accumulator
-    void* Y;                 // [ninst][N1][N2] column-pass output, row-major (j1 N2 + m2)
-    void* Z;                 // [ninst][N2][N1] row-pass output, column-major (m2 N1 + j1)
+    void* Y;                 // [ninst][N2][N1] column-pass output, column-major (m2 N1 + j1)
+    void* Z;                 // [ninst][N1][N2] row-pass output, row-major (j1 N2 + m2)
     const void* E;
     const void* e1;
     const void* e2;
@@ -97,11 +99,11 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
         w[j] = gload<T>(A.twN, ((long long)j1 * (t + j * P)) & (N - 1));
     pdl_wait();
     pdl_trigger();
-    const cx<T>* yrow = reinterpret_cast<const cx<T>*>(A.Y) + ibase + (long long)j1 * N2 + t;
+    const cx<T>* yrow = reinterpret_cast<const cx<T>*>(A.Y) + ibase + (long long)t * N1 + j1;
     cx<T> x[R];
 #pragma unroll
     for (int j = 0; j < R; ++j)
-        x[j] = yrow[j * P];
+        x[j] = yrow[(long long)j * P * N1];
     if (A.diag == LDIAG_IDFT) {
         grp.inverse(x, 0);
         if (valid) {
@@ -114,11 +116,11 @@ __global__ void __launch_bounds__(max_threads<LOGN2, R>()) large_row_kernel(cons
     }
     const T gN = (T)A.g0[inst] * ((T)1 / (T)N);   // N is a power of two: exact scaling
     grp.rhs(x, gN, cx<T>{T(0), T(0)});   // forward(i g0/N |a|^2 a) over j2, natural m2
-    cx<T>* zcol = reinterpret_cast<cx<T>*>(A.Z) + ibase + (long long)t * N1 + j1;
+    cx<T>* zcol = reinterpret_cast<cx<T>*>(A.Z) + ibase + (long long)j1 * N2 + t;
     if (valid) {
 #pragma unroll
         for (int j = 0; j < R; ++j)
-            zcol[(long long)j * P * N1] = cmulc(x[j], w[j]);   // * exp(-2 pi i j1 m2 / N)
+            zcol[j * P] = cmulc(x[j], w[j]);   // * exp(-2 pi i j1 m2 / N)
     }
 }
 
@@ -196,10 +198,10 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     cx<T> x[R];
     if constexpr (ST != LARGE_START) {
         // forward transform over j1 of Z column m2, as conj(inverse(conj(.)))
-        const cx<T>* z = reinterpret_cast<const cx<T>*>(A.Z) + e0;
+        const cx<T>* z = reinterpret_cast<const cx<T>*>(A.Z) + ibase + (long long)t * N2 + m2;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            const cx<T> v = z[j * estride];
+            const cx<T> v = z[(long long)j * P * N2];
             x[j] = {v.re, -v.im};
         }
         grp.inverse(x, 1);
@@ -293,10 +295,10 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
     // inverse transform over m1 of the next stage input, twiddle, store Y column m2
     grp.inverse(x, 0);
     if (valid) {
-        cx<T>* y = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)t * N2 + m2;
+        cx<T>* y = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)m2 * N1 + t;
 #pragma unroll
         for (int j = 0; j < R; ++j)
-            y[(long long)j * P * N2] = cmul(x[j], w[j]);   // * exp(+2 pi i j1 m2 / N)
+            y[j * P] = cmul(x[j], w[j]);   // * exp(+2 pi i j1 m2 / N)
     }
 }
 
@@ -311,10 +313,10 @@ __global__ void __launch_bounds__(max_threads<LOGN1, R>()) large_col_kernel(cons
 // them since the last barrier).  Every block must be resident at once: the host launches it
 // cooperatively, on request (persistent = 2) and only where the occupancy allows it.  The
 // arithmetic is that of the row and column kernels above, expression for expression, so both
-// paths give the same bits.  On N = 2^17 it takes 35.4 us per step against 34.8 for the kernel
+// paths give the same bits.  On N = 2^17 it takes 30.7 us per step against 29.6 for the kernel
 // sequence: a block spends its time at the barriers waiting for the slowest block and, in the
-// fence before its arrival, for its strided stores (ncu: barrier, long-scoreboard and membar
-// stalls first), as the kernels of the sequence wait for them at exit.
+// fence before its arrival, for its stores (ncu: barrier, long-scoreboard and membar stalls
+// first), as the kernels of the sequence wait for them at exit.
 //
 // Barrier: the block's threads synchronise; thread 0 issues a GPU-scope fence (cumulative over
 // the block's writes ordered before it by the block barrier), adds one arrival to a 64-bit
@@ -417,11 +419,12 @@ __global__ void __launch_bounds__(Plan<LOGN1, R>::P) large_grid_kernel(const Lar
         hh = 0.5 * A.h;
         h6 = A.h / 6.0;
     }
-    cx<T>* ycol = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)t * N2 + m2;
+    // Y column-major, Z row-major, as for the kernel sequence: contiguous stores
+    cx<T>* ycol = reinterpret_cast<cx<T>*>(A.Y) + ibase + (long long)m2 * N1 + t;
     const cx<T>* yrow = reinterpret_cast<const cx<T>*>(A.Y) + (long long)ri * N +
-                        (long long)j1 * N2 + tr;
-    cx<T>* zrow = reinterpret_cast<cx<T>*>(A.Z) + (long long)ri * N + (long long)tr * N1 + j1;
-    const cx<T>* zcol = reinterpret_cast<const cx<T>*>(A.Z) + e0;
+                        (long long)tr * N1 + j1;
+    cx<T>* zrow = reinterpret_cast<cx<T>*>(A.Z) + (long long)ri * N + (long long)j1 * N2 + tr;
+    const cx<T>* zcol = reinterpret_cast<const cx<T>*>(A.Z) + ibase + (long long)t * N2 + m2;
 
     const unsigned long long nb = gridDim.x;
     const int tries = A.bar_fault ? 1024 : (1 << 22);
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(Plan<LOGN1, R>::P) large_grid_kernel(const Lar
         gc.inverse(x, 0);
 #pragma unroll
         for (int j = 0; j < R; ++j)
-            ycol[(long long)j * PC * N2] = cmul(x[j], wc[j]);   // * exp(+2 pi i j1 m2 / N)
+            ycol[j * PC] = cmul(x[j], wc[j]);   // * exp(+2 pi i j1 m2 / N)
     };
 
     bool ok;
@@ -455,11 +458,11 @@ __global__ void __launch_bounds__(Plan<LOGN1, R>::P) large_grid_kernel(const Lar
                 cx<T> x[R];
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    x[j] = ldcg(yrow + j * PR);
+                    x[j] = ldcg(yrow + (long long)j * PR * N1);
                 gw.rhs(x, gNr, cx<T>{T(0), T(0)});
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    zrow[(long long)j * PR * N1] = cmulc(x[j], wr[j]);   // * exp(-2 pi i j1 m2/N)
+                    zrow[j * PR] = cmulc(x[j], wr[j]);   // * exp(-2 pi i j1 m2/N)
             }
             if (!(ok = barrier()))
                 break;
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(Plan<LOGN1, R>::P) large_grid_kernel(const Lar
             cx<T> x[R];
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                const cx<T> v = ldcg(zcol + j * PC);
+                const cx<T> v = ldcg(zcol + (long long)j * PC * N2);
                 x[j] = {v.re, -v.im};
             }
             gc.inverse(x, 1);
