@@ -175,14 +175,18 @@ void* cme_batch_stream(cme_batch b);
 
 /* The launch plan the library chose for launch group `group` (0-based, groups in increasing N):
  * N, values per thread, instances per block, blocks per instance (cluster) and the batch's
- * persistent mode (1 or 2).  Any output pointer may be NULL.  Errors: INVALID_ARG. */
+ * persistent mode (1 or 2; for N > 4096 groups 2 means the grid-barrier kernel, 1 the kernel
+ * sequence).  Any output pointer may be NULL.  Errors: INVALID_ARG. */
 int cme_batch_plan(cme_batch b, int group, int* N, int* radix, int* inst_per_cta, int* cluster,
                    int* persistent);
 
 /* Advance every instance by nsteps steps of size h (> 0) of the batch's integrator (Sec. 2:
  * RK4 or split step, with the FWM term evaluated through Eq. 4).  Asynchronous.  The first
  * call with a new h also recomputes the per-mode propagators exp(L h/2), expm1(L h/2),
- * expm1(L h) in FP64.  nsteps = 0 is a no-op.  Errors: INVALID_ARG, CUDA. */
+ * expm1(L h) in FP64.  Strang: within one launch the linear half flow that closes a step and
+ * the one that opens the next are applied as their exact composition over h, so n steps cost
+ * n + 1 linear flows; the result is that of n single steps up to rounding.  nsteps = 0 is a
+ * no-op.  Errors: INVALID_ARG, CUDA. */
 int cme_step(cme_batch b, double h, long nsteps);
 
 /* Pick the fastest launch plan for this batch and step size h by timing `probe_steps` steps of
