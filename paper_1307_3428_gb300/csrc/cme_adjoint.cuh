@@ -30,9 +30,10 @@ CME_DEV cx<T> cconj(cx<T> a) { return {a.re, -a.im}; }
 // Accumulator of one mode's L cotangent over the steps of a segment; the running total lives in
 // FP64 in memory between segments.  FP64 kernels continue the total term by term (so the sum,
 // and the gradient, do not depend on the segment length).  FP32 kernels keep the segment's
-// terms in a compensated float pair (exact two-sum per term) and add it to the total once per
+// terms in a compensated float pair and add it to the total once per
 // segment: FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU, and a convert-and-add
-// per term made it the bottleneck of the backward pass.
+// per term made it the bottleneck of the backward pass.  The pair is a Kahan sum (4 adds per
+// term, against 7 for an exact two-sum, on the backward pass's dependency chains).
 template <typename T>
 struct LAcc;
 template <>
@@ -48,22 +49,22 @@ struct LAcc<double> {
 };
 template <>
 struct LAcc<float> {
-    float hr, hi, lr, li;
-    CME_DEV void init(double2) { hr = hi = lr = li = 0.f; }
-    CME_DEV static void two_sum(float& h, float& l, float d)
+    float hr, hi, cr, ci;   // running sums and their Kahan compensations (minus the lost parts)
+    CME_DEV void init(double2) { hr = hi = cr = ci = 0.f; }
+    CME_DEV static void kahan(float& h, float& c, float d)
     {
-        const float s = h + d, b = s - h;
-        l += (h - (s - b)) + (d - b);
-        h = s;
+        const float y = d - c, t = h + y;
+        c = (t - h) - y;
+        h = t;
     }
     CME_DEV void add(cx<float> d)
     {
-        two_sum(hr, lr, d.re);
-        two_sum(hi, li, d.im);
+        kahan(hr, cr, d.re);
+        kahan(hi, ci, d.im);
     }
     CME_DEV double2 finish(double2 total) const
     {
-        return make_double2(total.x + ((double)hr + (double)lr), total.y + ((double)hi + (double)li));
+        return make_double2(total.x + ((double)hr - (double)cr), total.y + ((double)hi - (double)ci));
     }
 };
 
