@@ -622,15 +622,19 @@ CME_DEV void rk4ip_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs
 // resolved step.  For |y| <= 1/2 the Taylor series of sin (to y^9) and cos (to y^8), evaluated
 // in y^2 by Horner's rule, leave truncation errors below y^11/11! <= 1.2e-11 and
 // y^10/10! <= 2.7e-10, far under FP32 rounding; larger |y| take sincosf.
+CME_DEV void taylor_sincos(float y, float& s, float& c)
+{
+    const float y2 = y * y;
+    s = y * (1.f + y2 * (-1.f / 6 + y2 * (1.f / 120 + y2 * (-1.f / 5040 + y2 * (1.f / 362880)))));
+    c = 1.f + y2 * (-0.5f + y2 * (1.f / 24 + y2 * (-1.f / 720 + y2 * (1.f / 40320))));
+}
+CME_DEV bool small_phase(float y) { return fabsf(y) <= 0.5f; }   // false for NaN
 CME_DEV void small_sincos(float y, float& s, float& c)
 {
-    if (fabsf(y) <= 0.5f) {
-        const float y2 = y * y;
-        s = y * (1.f + y2 * (-1.f / 6 + y2 * (1.f / 120 + y2 * (-1.f / 5040 + y2 * (1.f / 362880)))));
-        c = 1.f + y2 * (-0.5f + y2 * (1.f / 24 + y2 * (-1.f / 720 + y2 * (1.f / 40320))));
-    } else {
+    if (small_phase(y))
+        taylor_sincos(y, s, c);
+    else
         sincosf(y, &s, &c);
-    }
 }
 
 // Linear and pump flow of the Strang step, exact, applied as the increment D += e D + c: over
@@ -678,17 +682,33 @@ CME_DEV void strang_kerr(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& f
             }
         }
         if (d == 0) {
+            // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h; the forward
+            // transform runs as conj(inverse(conj(.))).  FP32: the Taylor series for every
+            // value, then sincosf only for values outside its range, behind one branch per
+            // thread rather than one per value
+            T ph2[R], sn[R], cs[R];
+            bool big = false;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                // expm1(i phi) = (-2 sin^2(phi/2), sin(phi)), phi = g0 |a|^2 h; the forward
-                // transform runs as conj(inverse(conj(.)))
-                const T ph2 = c.g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
-                T s, co;
-                if constexpr (sizeof(T) == 4)
-                    small_sincos(ph2, s, co);
-                else
-                    sincos(ph2, &s, &co);
-                const cx<T> em = {T(-2) * s * s * invN, T(2) * s * co * invN};
+                ph2[j] = c.g0h * (x[j].re * x[j].re + x[j].im * x[j].im);
+                if constexpr (sizeof(T) == 4) {
+                    taylor_sincos(ph2[j], sn[j], cs[j]);
+                    big |= !small_phase(ph2[j]);
+                } else {
+                    sincos(ph2[j], &sn[j], &cs[j]);
+                }
+            }
+            if constexpr (sizeof(T) == 4) {
+                if (big) {
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        if (!small_phase(ph2[j]))
+                            sincosf(ph2[j], &sn[j], &cs[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cx<T> em = {T(-2) * sn[j] * sn[j] * invN, T(2) * sn[j] * cs[j] * invN};
                 const cx<T> b = cmul(x[j], em);
                 x[j] = {b.re, -b.im};
             }
