@@ -447,15 +447,35 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) strang_adjoint_kern
 #pragma unroll 1
         for (int p = 0; p < 2; ++p) {
             if (p == 1) {
+                // sin and cos of half the phase, as the forward step takes them (the Taylor
+                // series for every value, sincosf behind one branch per thread)
+                cx<T> avs[R];
+                T p2s[R], sns[R], css[R];
+                bool big = false;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    const cx<T> av = Dn[TT + j * P];
-                    const T p2 = av.re * av.re + av.im * av.im;
-                    T sn, cs;                                        // of half the phase
-                    if constexpr (sizeof(T) == 4)
-                        small_sincos(c.g0h * p2, sn, cs);
-                    else
-                        sincos(c.g0h * p2, &sn, &cs);
+                    avs[j] = Dn[TT + j * P];
+                    p2s[j] = avs[j].re * avs[j].re + avs[j].im * avs[j].im;
+                    if constexpr (sizeof(T) == 4) {
+                        taylor_sincos(c.g0h * p2s[j], sns[j], css[j]);
+                        big |= !small_phase(c.g0h * p2s[j]);
+                    } else {
+                        sincos(c.g0h * p2s[j], &sns[j], &css[j]);
+                    }
+                }
+                if constexpr (sizeof(T) == 4) {
+                    if (big) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j)
+                            if (!small_phase(c.g0h * p2s[j]))
+                                sincosf(c.g0h * p2s[j], &sns[j], &css[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const cx<T> av = avs[j];
+                    const T p2 = p2s[j];
+                    const T sn = sns[j], cs = css[j];
                     const T ph = gh * p2;                            // g0 h |a|^2
                     const T ur = T(1) - T(2) * sn * sn, ui = T(2) * sn * cs;
                     const cx<T> bb = cscale(z[j], invN);             // bbar

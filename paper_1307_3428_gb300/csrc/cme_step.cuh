@@ -621,7 +621,7 @@ CME_DEV void rk4ip_step(Group<T, LOGN, R, C>& grp, FieldState<T, LOGN, R, C>& fs
 // sin y and cos y in FP32 for the Strang Kerr phase y = g0 |a|^2 h / 2, which is small in any
 // resolved step.  For |y| <= 1/2 the Taylor series of sin (to y^9) and cos (to y^8), evaluated
 // in y^2 by Horner's rule, leave truncation errors below y^11/11! <= 1.2e-11 and
-// y^10/10! <= 2.7e-10, far under FP32 rounding; larger |y| take sincosf.
+// y^10/10! <= 2.7e-10, far under FP32 rounding; larger |y| (small_phase false) take sincosf.
 CME_DEV void taylor_sincos(float y, float& s, float& c)
 {
     const float y2 = y * y;
@@ -629,13 +629,6 @@ CME_DEV void taylor_sincos(float y, float& s, float& c)
     c = 1.f + y2 * (-0.5f + y2 * (1.f / 24 + y2 * (-1.f / 720 + y2 * (1.f / 40320))));
 }
 CME_DEV bool small_phase(float y) { return fabsf(y) <= 0.5f; }   // false for NaN
-CME_DEV void small_sincos(float y, float& s, float& c)
-{
-    if (small_phase(y))
-        taylor_sincos(y, s, c);
-    else
-        sincosf(y, &s, &c);
-}
 
 // Linear and pump flow of the Strang step, exact, applied as the increment D += e D + c: over
 // h/2 (full = false: e = expm1(L h/2), c = (exp(L_0 h/2) - 1)/L_0 sqrt(kappa_ext) A_in on the
