@@ -254,6 +254,7 @@ class Batch:
         self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
         self.total = int(self.offsets[-1])
         self.count = len(insts)
+        self.last_grad_schedule = None   # "stored" or "checkpoint" after a grad call
         self.precision = precision
         self.integrator = integrator
 
