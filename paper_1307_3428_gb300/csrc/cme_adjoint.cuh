@@ -349,8 +349,8 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                     const cx<T> k1b = caxpy(cscale(wb, h6), hh, xb);
                     const cx<T> y1 = ld(1, j);
                     const cx<T> D = ld(0, j);
-                    gl[j].add(cmulc(cmulc(ub[j], D), hE));       // conj(hh E) conj(D) ubar
-                    gl[j].add(cmulc(cmulc(k1b, y1), hE));        // conj(hh E) conj(y1) k1bar
+                    // conj(hh E) (conj(D) ubar + conj(y1) k1bar): one term, one sum
+                    gl[j].add(cmulc(cadd(cmulc(ub[j], D), cmulc(k1b, y1)), hE));
                     Db[j] = cmulc(ub[j], E);                     // conj(E) ubar
                     cot[j] = cmulc(k1b, E);                      // y1bar = conj(E) k1bar
                 }
