@@ -323,28 +323,41 @@ __global__ void __launch_bounds__(adj_threads<LOGN, R, C>()) adjoint_kernel(cons
                 grp.inverse(z, p);
             }
             grp.mask(z);   // nor does F depend on them: the VJP of m F(m x), m the mask
-            // z now holds conj(stage-input cotangent)
+            // z now holds conj(stage-input cotangent); one loop per stage, so that the stage
+            // test is taken once, not per value
+            if (st == 0) {
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const cx<T> xb = cconj(z[j]);
-                if (st == 0) {
-                    Db[j] = cadd(Db[j], xb);
-                    continue;
-                }
-                const cx<T> E = pr.getE(j);
-                const cx<T> wb = cmulc(Db[j], E);                // conj(E) Dbar'
-                const cx<T> hE = cscale(E, hh);
-                if (st == 3) {
+                for (int j = 0; j < R; ++j)
+                    Db[j] = cadd(Db[j], cconj(z[j]));
+            } else if (st == 3) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const cx<T> xb = cconj(z[j]);
+                    const cx<T> E = pr.getE(j);
+                    const cx<T> wb = cmulc(Db[j], E);            // conj(E) Dbar'
+                    const cx<T> hE = cscale(E, hh);
                     const cx<T> u = cmul(E, ld(0, j));
                     const cx<T> v = caxpy(u, h, ld(3, j));
                     const cx<T> vb = cmulc(xb, E);               // conj(E) x4bar
                     gl[j].add(cmulc(cmulc(xb, v), hE));          // conj(hh E) conj(v) x4bar
                     ub[j] = cadd(wb, vb);
                     cot[j] = caxpy(cscale(wb, h3), h, vb);       // k3bar
-                } else if (st == 2) {
+                }
+            } else if (st == 2) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const cx<T> xb = cconj(z[j]);
+                    const cx<T> wb = cmulc(Db[j], pr.getE(j));   // conj(E) Dbar'
                     ub[j] = cadd(ub[j], xb);
                     cot[j] = caxpy(cscale(wb, h3), hh, xb);      // k2bar
-                } else {   // st == 1
+                }
+            } else {   // st == 1
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const cx<T> xb = cconj(z[j]);
+                    const cx<T> E = pr.getE(j);
+                    const cx<T> wb = cmulc(Db[j], E);            // conj(E) Dbar'
+                    const cx<T> hE = cscale(E, hh);
                     ub[j] = cadd(ub[j], xb);
                     const cx<T> k1b = caxpy(cscale(wb, h6), hh, xb);
                     const cx<T> y1 = ld(1, j);
