@@ -65,7 +65,8 @@ typedef struct cme_batch_s* cme_batch;
 typedef struct cme_options {
     int precision;         /* CME_FP64 or CME_FP32 */
     int integrator;        /* CME_RK4IP or CME_STRANG */
-    int radix;             /* field elements per thread (4, 8 or 16); 0 = library choice.
+    int radix;             /* field elements per thread (4, 8 or 16; 2 at N = 64, 128);
+                              0 = library choice.
                               For N > 4096, 4 selects the row and column kernels at 4 values
                               per thread where compiled (N1, N2 in 2^8 ... 2^10), else 8 */
     int inst_per_cta;      /* instances sharing one thread block; 0 = library choice */

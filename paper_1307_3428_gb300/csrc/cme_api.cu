@@ -108,9 +108,10 @@ void dev_free(void* p, cme_free_fn f, void* ctx)
 bool shape_compiled(int logN, int R)
 {
     static const int shapes[][2] = {{2, 4},  {3, 8},  {4, 8},  {4, 16}, {5, 8},  {5, 16},
-                                    {6, 8},  {6, 4},  {6, 16}, {7, 8},  {7, 4},  {7, 16},
-                                    {8, 8},  {8, 4},  {8, 16}, {9, 8},  {9, 4},  {10, 8},
-                                    {10, 4}, {11, 8}, {11, 16}, {12, 8}, {12, 16}};
+                                    {6, 8},  {6, 4},  {6, 16}, {6, 2},  {7, 8},  {7, 4},
+                                    {7, 16}, {7, 2},  {8, 8},  {8, 4},  {8, 16}, {9, 8},
+                                    {9, 4},  {10, 8}, {10, 4}, {11, 8}, {11, 16}, {12, 8},
+                                    {12, 16}};
     for (auto& s : shapes)
         if (s[0] == logN && s[1] == R)
             return true;
@@ -122,13 +123,18 @@ bool shape_compiled(int logN, int R)
 // step at N = 4096 and 7.2 against 7.4 at N = 2048 (GB300).
 // FP64 groups too small to give every SM a warp at 8 values per thread take 4: each thread's
 // chain of FP64 instructions (1/64 of the FP32 rate) then sets the step time, and halving it
-// measured 31 against 55 us per step for one N = 64 instance.  sms = 0: no such information.
+// measured 31 against 55 us per step for one N = 64 instance.  Groups of N = 64 or 128 that
+// hold at most one warp per SM at 2 values per thread take 2, halving the chain again: 19.4
+// against 31 us per step for one N = 64 instance.  sms = 0: no such information.
 int default_radix(int logN, int prec, int count = 0, int sms = 0)
 {
     if (logN <= 2)
         return 4;
     if (prec == PREC_FP32 && logN >= 11)
         return 16;
+    if (prec == PREC_FP64 && sms > 0 && shape_compiled(logN, 2) &&
+        (long long)count * ((1 << logN) / 2) <= 32LL * sms)
+        return 2;
     if (prec == PREC_FP64 && sms > 0 && shape_compiled(logN, 4) &&
         (long long)count * ((1 << logN) / 8) < 32LL * sms)
         return 4;
@@ -1365,7 +1371,7 @@ int cme_autotune(cme_batch b, double h, long probe_steps, cme_options* plan_out)
     base.steps_per_launch = 0;
     if (b->groups.size() == 1) {
         const auto& g = b->groups[0];
-        for (int R : {4, 8, 16}) {
+        for (int R : {2, 4, 8, 16}) {
             if (R > g.N || !shape_compiled(g.logN, R))
                 continue;
             for (int G : {0, 2, 4}) {

@@ -8,14 +8,15 @@
 namespace cme {
 
 // Every compiled (log2 N, values per thread) pair.  Values per thread R: 8 is the default;
-// 4 and 16 are alternative launch shapes where they fit in registers without spilling.
+// 4 and 16 are alternative launch shapes where they fit in registers without spilling, and 2
+// serves single FP64 instances of N = 64, 128 (the shortest chain of FP64 instructions).
 #define CME_FOR_EACH_SHAPE(X)          \
     X(2, 4)                            \
     X(3, 8)                            \
     X(4, 8) X(4, 16)                   \
     X(5, 8) X(5, 16)                   \
-    X(6, 8) X(6, 4) X(6, 16)           \
-    X(7, 8) X(7, 4) X(7, 16)           \
+    X(6, 8) X(6, 4) X(6, 16) X(6, 2)   \
+    X(7, 8) X(7, 4) X(7, 16) X(7, 2)   \
     X(8, 8) X(8, 4) X(8, 16)           \
     X(9, 8) X(9, 4)                    \
     X(10, 8) X(10, 4)                  \

@@ -232,6 +232,25 @@ def test_radix_variants_agree(radix):
         assert rel(g, r) <= 1e-12
 
 
+@pytest.mark.parametrize("N", [64, 128])
+def test_two_values_per_thread_fp64(N):
+    """Small FP64 groups of N = 64, 128 take 2 values per thread by default (one warp per
+    instance at N = 64: the shortest chain of FP64 instructions per thread); every values-per-
+    thread choice agrees with the Eq. 4 engine, for RK4IP and Strang."""
+    amp = 0.3 * min(1.0, np.sqrt(64.0 / N))
+    insts = [wl.random_instance(N, 700 + k, amp=amp, sigma=0.4 * k, A_in=1.2 + 0.1j * k)
+             for k in range(3)]
+    assert batch_of(insts[:1], cme.FP64).plan(0)["radix"] == 2
+    assert batch_of(insts[:1], cme.FP32).plan(0)["radix"] == 8
+    for integ, engine in ((cme.RK4IP, fft_engine.rk4ip), (cme.STRANG, fft_engine.strang)):
+        refs = engine(fft_engine.Batch(insts), 1e-3, 40)
+        for radix in (2, 4, 8):
+            b = batch_of(insts, cme.FP64, integ, radix=radix)
+            b.step(1e-3, 40)
+            for g, r in zip(b.split(b.get_state()), refs):
+                assert rel(g, r) <= 1e-12, (integ, radix)
+
+
 def test_uneven_sizes_in_one_batch():
     insts = [wl.random_instance(N, 1300 + N, amp=0.2 * min(1.0, np.sqrt(64.0 / N)))
              for N in (4, 16, 16, 64, 256, 256, 1024)]
