@@ -277,9 +277,10 @@ int inst_per_block(int N, int R, int G, int count)
     if (P < 32) {
         // groups narrower than a warp synchronise with __syncwarp over full warps: make the
         // block a whole number of warps (surplus groups recompute the last instance and store
-        // nothing)
+        // nothing), and no more warps than the instances fill
         const int per_warp = 32 / P;
-        return std::max(per_warp, (G + per_warp - 1) / per_warp * per_warp);
+        const int g = std::min(G, std::max(count, 1));
+        return (g + per_warp - 1) / per_warp * per_warp;
     }
     return std::min(G, count);
 }

@@ -251,6 +251,22 @@ def test_two_values_per_thread_fp64(N):
                 assert rel(g, r) <= 1e-12, (integ, radix)
 
 
+def test_narrow_groups_fill_no_more_warps_than_instances():
+    """Groups narrower than a warp fill whole warps, but no more of them than the instances
+    need: one N = 16 instance runs as one warp (16 groups of 2 threads, 15 of them surplus),
+    and its result is bit for bit that of the same instance in a fuller block."""
+    insts = [wl.random_instance(16, 500 + k, amp=0.3, sigma=0.3 * k, A_in=1.1) for k in range(40)]
+    for prec in (cme.FP32, cme.FP64):
+        one = batch_of(insts[:1], prec)
+        p = one.plan(0)
+        assert p["inst_per_cta"] * (16 // p["radix"]) == 32, p
+        many = batch_of(insts, prec)
+        assert many.plan(0)["inst_per_cta"] > p["inst_per_cta"]
+        for b in (one, many):
+            b.step(1e-3, 30)
+        assert np.array_equal(one.get_state(), many.get_state()[:16]), prec
+
+
 def test_uneven_sizes_in_one_batch():
     insts = [wl.random_instance(N, 1300 + N, amp=0.2 * min(1.0, np.sqrt(64.0 / N)))
              for N in (4, 16, 16, 64, 256, 256, 1024)]
