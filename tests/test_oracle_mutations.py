@@ -3,7 +3,7 @@
 index or sign, a dropped or wrong Runge-Kutta term, the pump on the wrong mode, a wrong
 normalisation, a wrong mode band, a wrong step in the adjoint), compiles it with the oracle's
 own flags, and runs the committed pin suites (test_oracle_pins, test_oracle_adjoint,
-test_oracle_padding, test_oracle_kerr) in a child process whose oracle calls all go to the modified build.  The
+test_oracle_tangent, test_oracle_padding, test_oracle_kerr) in a child process whose oracle calls all go to the modified build.  The
 same is done for the oracle's numpy Eq. 4 engine (`oracle/fft_engine.py`) through a copy of the
 package.  The unmodified sources must pass the pins; every mutant must fail at least one.
 CPU only."""
@@ -16,7 +16,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "cme_oracle.c")
 PIN_SUITES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py",
-              "tests/test_oracle_padding.py", "tests/test_oracle_kerr.py"]
+              "tests/test_oracle_tangent.py", "tests/test_oracle_padding.py",
+              "tests/test_oracle_kerr.py"]
 
 # name: (text in cme_oracle.c, replacement); the text occurs exactly once.
 MUTATIONS = {
@@ -80,6 +81,12 @@ MUTATIONS = {
     "adjoint: propagator cotangent": ("const cplx Lb = conj(0.5 * h * E[i]) * Eb[i];",
                                       "const cplx Lb = conj(h * E[i]) * Eb[i];"),
     "adjoint: pump cotangent conjugated": ("*pbar += ybar[N / 2];", "*pbar += conj(ybar[N / 2]);"),
+    "adjoint: propagator cotangent of k1 = E y1 dropped": (
+        "            Eb[i] += conj(y1[i]) * kb[i];\n", ""),
+    "adjoint: propagator cotangent of the last stage dropped": (
+        "            Eb[i] += conj(v[i]) * xb[i];\n", ""),
+    "adjoint: k1 cotangent weight": ("kb[i] = h / 6.0 * wb[i] + 0.5 * h * xb[i]; /* k1bar */",
+                                     "kb[i] = h / 3.0 * wb[i] + 0.5 * h * xb[i]; /* k1bar */"),
     # adjoint of the Strang split step
     "Strang adjoint: phase factor not conjugated": (
         "ab[j] = conj(u[j]) * (1.0 - I * gam * p2) * bb[j] +",
