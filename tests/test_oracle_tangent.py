@@ -5,8 +5,8 @@ picture, the Strang split step with the exact Kerr phase and the exact affine li
 with the four-wave-mixing sum evaluated through numpy's FFT (Eq. 4) -- gives J v up to
 rounding.  The oracle's adjoint gives J^H w for the loss cotangent w of the final field.  So
 Re <w, J v> = Re <J^H w, v> must hold to rounding, for directions of the initial field and for
-the parameters sigma, A_in, D2, D3 and kappa: a far tighter pin than finite differences.
-CPU only."""
+the parameters sigma, A_in, D2, D3 and kappa, with padding modes, the linear (de-aliased) sum
+and per-mode Kerr coefficients: a far tighter pin than finite differences.  CPU only."""
 import numpy as np
 import pytest
 
@@ -14,19 +14,48 @@ import oracle
 from paper_1307_3428_gb300 import workloads as wl
 
 
-def fwm(D):
-    """Eq. 4 in centred order: a = unnormalised inverse DFT over mu, FWM = DFT(|a|^2 a) / N."""
-    N = D.size
-    a = N * np.fft.ifft(np.fft.ifftshift(D))
+def _eq4(x, linear):
+    """Circular FWM sum of a centred vector through Eq. 4 (a = unnormalised inverse DFT over
+    mu, FWM = DFT(|a|^2 a) / N), or the linear (non-wrapping) sum: the circular sum of the
+    vector embedded in 2N slots, whose central N entries no wrapped triple reaches."""
+    N = x.size
+    if linear:
+        z = np.zeros(2 * N, complex)
+        z[N // 2:N // 2 + N] = x
+        return _eq4(z, False)[N // 2:N // 2 + N]
+    a = N * np.fft.ifft(np.fft.ifftshift(x))
     return np.fft.fftshift(np.fft.fft(np.abs(a) ** 2 * a)) / N
 
 
-def fwm_jvp(D, dD):
-    """Directional derivative of fwm at D along dD: d(|a|^2 a) = 2 |a|^2 da + a^2 conj(da)."""
-    N = D.size
-    a = N * np.fft.ifft(np.fft.ifftshift(D))
-    da = N * np.fft.ifft(np.fft.ifftshift(dD))
+def _eq4_jvp(x, dx, linear):
+    """Directional derivative of _eq4 at x along dx: d(|a|^2 a) = 2 |a|^2 da + a^2 conj(da)."""
+    N = x.size
+    if linear:
+        z, dz = np.zeros(2 * N, complex), np.zeros(2 * N, complex)
+        z[N // 2:N // 2 + N], dz[N // 2:N // 2 + N] = x, dx
+        return _eq4_jvp(z, dz, False)[N // 2:N // 2 + N]
+    a = N * np.fft.ifft(np.fft.ifftshift(x))
+    da = N * np.fft.ifft(np.fft.ifftshift(dx))
     return np.fft.fftshift(np.fft.fft(2 * np.abs(a) ** 2 * da + a * a * np.conj(da))) / N
+
+
+def mask_of(inst):
+    """Physical modes: the centred M of the N (all N without padding)."""
+    N = inst.N
+    M = getattr(inst, "M", None) or N
+    i = np.arange(N)
+    return (i >= N // 2 - M // 2) & (i < N // 2 - M // 2 + M)
+
+
+def fwm(D, m=None, linear=False):
+    """FWM sum over the physical modes m, zero on the others."""
+    m = np.ones(D.size, bool) if m is None else m
+    return np.where(m, _eq4(np.where(m, D, 0), linear), 0)
+
+
+def fwm_jvp(D, dD, m=None, linear=False):
+    m = np.ones(D.size, bool) if m is None else m
+    return np.where(m, _eq4_jvp(np.where(m, D, 0), np.where(m, dD, 0), linear), 0)
 
 
 def operator(inst):
@@ -38,23 +67,25 @@ def operator(inst):
     return L, P
 
 
-def rk4ip_tangent(inst, h, n, dD0, dL, dP):
+def rk4ip_tangent(inst, h, n, dD0, dL, dP, linear=False):
     """n RK4IP steps (E = exp(L h / 2); k1 = E F(D), k2 = F(E D + h/2 k1), k3 = F(E D + h/2 k2),
-    k4 = F(E (E D + h k3)), D' = E (E D + h/6 (k1 + 2 k2 + 2 k3)) + h/6 k4, F = P + i g0 FWM)
-    with the tangent of every quantity along (dD0, dL, dP)."""
+    k4 = F(E (E D + h k3)), D' = E (E D + h/6 (k1 + 2 k2 + 2 k3)) + h/6 k4, F = P + i g0 FWM,
+    g0 per output mode where the instance has per-mode coefficients; padding modes start at
+    zero and receive no FWM term) with the tangent of every quantity along (dD0, dL, dP)."""
     L, P = operator(inst)
-    g0 = inst.g0
+    m = mask_of(inst)
+    g = inst.g0 if getattr(inst, "g0_mu", None) is None else np.asarray(inst.g0_mu)
     E = np.exp(0.5 * h * L)
     dE = 0.5 * h * dL * E
 
     def F(x):
-        return P + 1j * g0 * fwm(x)
+        return P + 1j * g * fwm(x, m, linear)
 
     def dF(x, dx):
-        return dP + 1j * g0 * fwm_jvp(x, dx)
+        return dP + 1j * g * fwm_jvp(x, dx, m, linear)
 
-    D = np.array(inst.D0, complex)
-    dD = np.array(dD0, complex)
+    D = np.where(m, np.array(inst.D0, complex), 0)
+    dD = np.where(m, np.array(dD0, complex), 0)
     for _ in range(n):
         AI, dAI = E * D, dE * D + E * dD
         f1 = F(D)
@@ -72,11 +103,14 @@ def rk4ip_tangent(inst, h, n, dD0, dL, dP):
     return D, dD
 
 
-def strang_tangent(inst, h, n, dD0, dL, dP):
+def strang_tangent(inst, h, n, dD0, dL, dP, linear=False):
     """n Strang steps (exact linear+pump flow over h/2, D -> E D + c on mode 0 with
     c = (E_0 - 1) / L_0 P_0; exact Kerr flow a -> a exp(i g0 |a|^2 h) of a = IDFT(D), D = DFT(a)/N;
-    the linear flow again) with the tangent of every quantity along (dD0, dL, dP)."""
+    the linear flow again; padding modes start at zero and the Kerr flow leaves them there)
+    with the tangent of every quantity along (dD0, dL, dP)."""
+    assert not linear
     L, P = operator(inst)
+    m = mask_of(inst)
     N, c, g0 = inst.N, inst.N // 2, inst.g0
     E = np.exp(0.5 * h * L)
     dE = 0.5 * h * dL * E
@@ -84,7 +118,7 @@ def strang_tangent(inst, h, n, dD0, dL, dP):
     c0 = (E0 - 1.0) / L0 * P[c]
     dc0 = ((0.5 * h * dL[c] * E0) / L0 - (E0 - 1.0) * dL[c] / L0 ** 2) * P[c] + (E0 - 1.0) / L0 * dP[c]
 
-    def linear(D, dD):
+    def half_flow(D, dD):
         D1, dD1 = E * D, dE * D + E * dD
         D1[c] += c0
         dD1[c] += dc0
@@ -96,14 +130,15 @@ def strang_tangent(inst, h, n, dD0, dL, dP):
         u = np.exp(1j * g0 * h * np.abs(a) ** 2)
         dph = g0 * h * 2.0 * np.real(np.conj(a) * da)
         b, db = a * u, u * (da + 1j * a * dph)
-        return (np.fft.fftshift(np.fft.fft(b)) / N, np.fft.fftshift(np.fft.fft(db)) / N)
+        return (np.where(m, np.fft.fftshift(np.fft.fft(b)) / N, 0),
+                np.where(m, np.fft.fftshift(np.fft.fft(db)) / N, 0))
 
-    D = np.array(inst.D0, complex)
-    dD = np.array(dD0, complex)
+    D = np.where(m, np.array(inst.D0, complex), 0)
+    dD = np.where(m, np.array(dD0, complex), 0)
     for _ in range(n):
-        D, dD = linear(D, dD)
+        D, dD = half_flow(D, dD)
         D, dD = kerr(D, dD)
-        D, dD = linear(D, dD)
+        D, dD = half_flow(D, dD)
     return D, dD
 
 
@@ -127,29 +162,52 @@ def _target(N, seed):
 
 METHODS = {oracle.RK4IP: rk4ip_tangent, oracle.STRANG: strang_tangent}
 
+# (integrator, N, physical modes M, linear sum, per-mode Kerr coefficients)
+CASES = [
+    (oracle.RK4IP, 8, None, False, False),
+    (oracle.RK4IP, 16, None, False, False),
+    (oracle.RK4IP, 16, 13, False, False),
+    (oracle.RK4IP, 8, None, True, False),
+    (oracle.RK4IP, 16, None, False, True),
+    (oracle.RK4IP, 16, 11, True, True),
+    (oracle.STRANG, 8, None, False, False),
+    (oracle.STRANG, 16, None, False, False),
+    (oracle.STRANG, 16, 13, False, False),
+]
 
-def test_tangent_model_forward_matches_the_oracle():
-    """The model's own forward run is the oracle's (its FWM is the direct sum's, Eq. 4 = Eq. 3)."""
-    inst = _instance(16, 3)
-    D = np.random.default_rng(4).standard_normal(16) * (1 + 1j)
-    assert np.max(np.abs(fwm(D) - oracle.fwm(D))) <= 1e-12 * np.max(np.abs(oracle.fwm(D)))
-    z = np.zeros(16, complex)
-    for method, run in METHODS.items():
-        got, _ = run(inst, 0.02, 30, z, z, z)
-        ref = oracle.integrate(inst, 0.02, 30, method)
-        assert oracle.rel_l2(got, ref) <= 1e-12, method
+
+def _case(N, M, kerr, seed):
+    inst = _instance(N, seed)
+    if M:
+        inst.M = M
+    if kerr:
+        inst.g0_mu = np.random.default_rng(seed + 2).uniform(0.5, 1.5, N)
+    return inst
 
 
-@pytest.mark.parametrize("method", [oracle.RK4IP, oracle.STRANG])
-@pytest.mark.parametrize("N", [8, 16])
-def test_adjoint_dot_product(method, N):
+@pytest.mark.parametrize("method,N,M,linear,kerr", CASES)
+def test_tangent_model_forward_matches_the_oracle(method, N, M, linear, kerr):
+    """The model's own forward run is the oracle's (its FWM is the direct sum's: Eq. 4 = Eq. 3,
+    over the physical modes, circular or linear)."""
+    inst = _case(N, M, kerr, 3 + N)
+    D = np.random.default_rng(4).standard_normal(N) * (1 + 1j)
+    m = mask_of(inst)
+    ref = oracle.fwm(D, linear, M)
+    assert np.max(np.abs(fwm(D, m, linear) - ref)) <= 1e-12 * np.max(np.abs(ref))
+    z = np.zeros(N, complex)
+    got, _ = METHODS[method](inst, 0.02, 30, z, z, z, linear)
+    assert oracle.rel_l2(got, oracle.integrate(inst, 0.02, 30, method, linear)) <= 1e-12
+
+
+@pytest.mark.parametrize("method,N,M,linear,kerr", CASES)
+def test_adjoint_dot_product(method, N, M, linear, kerr):
     h, n, eps = 0.02, 40, 1e-20
-    inst = _instance(N, 20 + N)
+    inst = _case(N, M, kerr, 20 + N)
     T = _target(N, 30 + N)
-    g = oracle.log_spectrum_grad(inst, h, n, T, eps=eps, method=method)
+    g = oracle.log_spectrum_grad(inst, h, n, T, eps=eps, linear=linear, method=method)
     run = METHODS[method]
     z = np.zeros(N, complex)
-    Dn, _ = run(inst, h, n, z, z, z)
+    Dn, _ = run(inst, h, n, z, z, z, linear)
     w = loss_cotangent(Dn, T, eps)
     mu = (np.arange(N) - N // 2).astype(float)
     c = N // 2
@@ -157,7 +215,7 @@ def test_adjoint_dot_product(method, N):
     e0[c] = np.sqrt(inst.kappa_ext)
 
     def directional(dD0=z, dL=z, dP=z):
-        _, dDn = run(inst, h, n, dD0, dL, dP)
+        _, dDn = run(inst, h, n, dD0, dL, dP, linear)
         return float(np.real(np.vdot(w, dDn)))
 
     scale = np.max(np.abs(g["D0"]))
