@@ -7,11 +7,14 @@ kernels' address arithmetic restated (the transform code of csrc/cme_core.cuh):
   at every N and values per thread R the kernels compile;
 - XOR layout p -> p ^ (8 bit6(p)) of the exchange after a radix-8 pass of stride 8: the two
   per-thread bases of the kernels give exactly that map, it is a bijection, and each
-  half-warp's writes and reads hit 16 distinct 8-byte banks.
+  half-warp's writes and reads hit 16 distinct 8-byte banks;
+- the passes themselves (butterfly slots, twiddle indices, exchange positions) compose to the
+  unnormalised inverse DFT for every compiled transform shape.
 CPU only."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -102,3 +105,42 @@ def test_xor_layout_of_the_stride_8_exchange(logn):
             writes = {xor8(64 * (t >> 3) + (t & 7) + 8 * j) % 16 for t in ts}
             reads = {xor8(t + j * p) % 16 for t in ts}
             assert len(writes) == 16 and len(reads) == 16, (h, j)
+
+
+@pytest.mark.parametrize("logn,r", compiled_transforms())
+def test_stockham_passes_and_twiddles(logn, r):
+    """The in-block transform as the kernels run it: thread t holds positions t + j P; pass s
+    (radix r_s, stride L = R^s, Q = R / r_s butterflies a thread) takes butterfly q from slots
+    q + j Q, multiplies element j by the table entry (j k N / (L r_s)) mod N with
+    k = (t + q P) mod L (exp(2 pi i j k / (L r_s))), runs the r_s-point transform, and (except
+    after the last pass) writes slot j to position (t - k) R + k + j L and reads back t + j P.
+    The result, in positions t + j P, is the unnormalised inverse DFT."""
+    n, p, ns, logr = plan(logn, r)
+    log_last = logn - (ns - 1) * logr
+    tw = np.exp(2j * np.pi * np.arange(n) / n)
+    X = np.array([1, 1j]) @ np.random.default_rng(logn * 17 + r).standard_normal((2, n))
+    x = np.array([[X[t + j * p] for j in range(r)] for t in range(p)])
+    for s in range(ns):
+        rs = r if s < ns - 1 else 1 << log_last
+        Q, L = r // rs, 1 << (s * logr)
+        stride = n // (L * rs)
+        for t in range(p):
+            for q in range(Q):
+                v = x[t, q + Q * np.arange(rs)]
+                if s > 0:
+                    k = (t + q * p) & (L - 1)
+                    v = v * tw[(np.arange(rs) * k * stride) % n]
+                x[t, q + Q * np.arange(rs)] = rs * np.fft.ifft(v)
+        if s + 1 < ns:
+            buf = np.full(n, np.nan + 0j)
+            for t in range(p):
+                k = t & (L - 1)
+                pos = (t - k) * r + k + np.arange(r) * L
+                assert np.all(np.isnan(buf[pos]))
+                buf[pos] = x[t]
+            x = np.array([[buf[t + j * p] for j in range(r)] for t in range(p)])
+    out = np.empty(n, complex)
+    for t in range(p):
+        out[t + p * np.arange(r)] = x[t]
+    ref = n * np.fft.ifft(X)
+    assert np.max(np.abs(out - ref)) <= 1e-9 * np.max(np.abs(ref))
