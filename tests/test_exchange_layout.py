@@ -129,7 +129,13 @@ def test_stockham_passes_and_twiddles(logn, r):
                 v = x[t, q + Q * np.arange(rs)]
                 if s > 0:
                     k = (t + q * p) & (L - 1)
-                    v = v * tw[(np.arange(rs) * k * stride) % n]
+                    idx = (np.arange(rs) * k * stride) % n
+                    # the table-read variant (large N): k_s = (t mod L) N / (L r_s) per pass,
+                    # and butterflies q > 0 only in the last pass, where k = t + q P exactly
+                    kst = (t & (L - 1)) * stride
+                    assert np.array_equal(idx, (np.arange(rs) * kst
+                                                + np.arange(rs) * q * p * stride) % n)
+                    v = v * tw[idx]
                 x[t, q + Q * np.arange(rs)] = rs * np.fft.ifft(v)
         if s + 1 < ns:
             buf = np.full(n, np.nan + 0j)
